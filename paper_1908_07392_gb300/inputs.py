@@ -1,0 +1,326 @@
+"""Seeded synthetic inputs for the volume-potential workloads.
+
+This module prepares inputs only: quadtrees (uniform, or refined on the
+resolution of the source and then 2:1 balanced), the tensor Gauss-Legendre
+node coordinates at which the source is sampled, and the source functions.
+It holds none of the volume-potential arithmetic, so both the oracle and the
+CUDA path can consume what it produces.
+
+Geometry conventions shared by every consumer (they define the input format):
+
+* root box: centre (cx, cy), side length ``side``;
+* a leaf is (level, ix, iy): side h = side / 2**level, lower-left corner
+  (cx - side/2 + ix*h, cy - side/2 + iy*h);
+* each leaf carries p x p Gauss-Legendre nodes; the node with x-index i and
+  y-index j has flat index j*p + i within the leaf, and leaves are stored in
+  the order given, so a field has shape [n_leaves * p * p].
+
+The quadtree is level-restricted (adjacent leaves differ by at most one
+level), as the paper's fast-summation section requires of its trees.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable
+
+import numpy as np
+
+KERNEL_MHELMHOLTZ = 0   # G1(r) = K0(alpha r) / (2 pi)
+KERNEL_MBIHARMONIC = 1  # G2(r) = (K0(alpha r) + log r) / (2 pi alpha^2)
+
+
+@dataclasses.dataclass
+class Tree:
+    """Leaf list of a level-restricted quadtree over a square root box."""
+    cx: float
+    cy: float
+    side: float
+    level: np.ndarray  # int32 [n_leaves]
+    ix: np.ndarray     # int32 [n_leaves]
+    iy: np.ndarray     # int32 [n_leaves]
+
+    @property
+    def n_leaves(self) -> int:
+        return int(self.level.shape[0])
+
+    @property
+    def max_level(self) -> int:
+        return int(self.level.max()) if self.n_leaves else 0
+
+    def leaf_boxes(self):
+        """(x0, y0, h) arrays: lower-left corners and sides of the leaves."""
+        h = self.side / (2.0 ** self.level.astype(np.float64))
+        x0 = self.cx - self.side / 2 + self.ix * h
+        y0 = self.cy - self.side / 2 + self.iy * h
+        return x0, y0, h
+
+
+@dataclasses.dataclass
+class Workload:
+    """One volume-potential problem: kernel, alpha, p, tree and sampled source."""
+    name: str
+    kernel: int
+    alpha: float
+    p: int
+    tree: Tree
+    f: np.ndarray          # float64 [n_leaves * p * p]
+    source: Callable | None = None
+
+    @property
+    def n_nodes(self) -> int:
+        return self.tree.n_leaves * self.p * self.p
+
+
+def gl_nodes(p: int):
+    """Gauss-Legendre nodes and weights on [-1, 1] (ascending)."""
+    x, w = np.polynomial.legendre.leggauss(p)
+    return x, w
+
+
+def node_coords(tree: Tree, p: int):
+    """Coordinates (x, y) of every leaf node, in the storage order above."""
+    xi, _ = gl_nodes(p)
+    x0, y0, h = tree.leaf_boxes()
+    t = (xi + 1.0) / 2.0
+    X = x0[:, None, None] + h[:, None, None] * t[None, None, :]   # [L, j, i]
+    Y = y0[:, None, None] + h[:, None, None] * t[None, :, None]
+    X = np.broadcast_to(X, (tree.n_leaves, p, p))
+    Y = np.broadcast_to(Y, (tree.n_leaves, p, p))
+    return np.ascontiguousarray(X).reshape(-1), np.ascontiguousarray(Y).reshape(-1)
+
+
+# --------------------------------------------------------------------------
+# trees
+
+def uniform_tree(depth: int, cx=0.0, cy=0.0, side=2.0) -> Tree:
+    n = 1 << depth
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    return Tree(cx, cy, side,
+                np.full(n * n, depth, np.int32),
+                ii.reshape(-1).astype(np.int32), jj.reshape(-1).astype(np.int32))
+
+
+def _children(l, x, y):
+    return [(l + 1, 2 * x + a, 2 * y + b) for b in (0, 1) for a in (0, 1)]
+
+
+def balance_21(leaves: set) -> set:
+    """Refine leaves until adjacent leaves differ by at most one level."""
+    leaves = set(leaves)
+    while True:
+        internal = set()
+        for (l, x, y) in leaves:
+            while l > 0:
+                l, x, y = l - 1, x >> 1, y >> 1
+                if (l, x, y) in internal:
+                    break
+                internal.add((l, x, y))
+        to_split = []
+        for (l, x, y) in leaves:
+            n1 = 1 << (l + 1)
+            bx, by = 2 * x, 2 * y
+            hit = False
+            for a in (-1, 0, 1, 2):
+                for b in (-1, 0, 1, 2):
+                    if 0 <= a <= 1 and 0 <= b <= 1:
+                        continue
+                    X, Y = bx + a, by + b
+                    if 0 <= X < n1 and 0 <= Y < n1 and (l + 1, X, Y) in internal:
+                        hit = True
+                        break
+                if hit:
+                    break
+            if hit:
+                to_split.append((l, x, y))
+        if not to_split:
+            return leaves
+        for b in to_split:
+            leaves.discard(b)
+            leaves.update(_children(*b))
+
+
+def legendre_tail(F: np.ndarray, p: int) -> np.ndarray:
+    """Largest tensor Legendre coefficient with i+j >= p-2, per leaf.
+
+    F has shape [L, p(j), p(i)] holding samples at the Gauss-Legendre nodes.
+    """
+    x, w = gl_nodes(p)
+    k = np.arange(p)
+    Pk = np.polynomial.legendre.legvander(x, p - 1)          # [node, k]
+    A = (Pk * w[:, None]).T * ((2 * k + 1) / 2.0)[:, None]   # [k, node]
+    C = np.einsum("ai,lji,bj->lba", A, F, A)                  # [L, kj, ki]
+    mask = (k[:, None] + k[None, :]) >= p - 2
+    return np.abs(C[:, mask]).max(axis=1)
+
+
+def adaptive_tree(fn, p: int, cx: float, cy: float, side: float, tol: float,
+                  max_depth: int, min_depth: int = 2, fscale: float | None = None) -> Tree:
+    """Refine until every leaf's Legendre tail / ||f||_inf is below tol, then 2:1 balance."""
+    xi, _ = gl_nodes(p)
+    t = (xi + 1.0) / 2.0
+    active = [(min_depth, x, y) for y in range(1 << min_depth) for x in range(1 << min_depth)]
+    done = []
+    if fscale is None:
+        n = 512
+        g = cx - side / 2 + side * (np.arange(n) + 0.5) / n
+        GX, GY = np.meshgrid(g, g)
+        fscale = float(np.abs(fn(GX, GY)).max()) or 1.0
+    while active:
+        arr = np.array(active, dtype=np.int64)
+        l, x, y = arr[:, 0], arr[:, 1], arr[:, 2]
+        h = side / (2.0 ** l)
+        x0 = cx - side / 2 + x * h
+        y0 = cy - side / 2 + y * h
+        X = x0[:, None, None] + h[:, None, None] * t[None, None, :]
+        Y = y0[:, None, None] + h[:, None, None] * t[None, :, None]
+        F = fn(np.broadcast_to(X, (len(active), p, p)), np.broadcast_to(Y, (len(active), p, p)))
+        tail = legendre_tail(F, p) / fscale
+        nxt = []
+        for k, b in enumerate(active):
+            if tail[k] > tol and b[0] < max_depth:
+                nxt.extend(_children(*b))
+            else:
+                done.append(b)
+        active = nxt
+    leaves = balance_21(set(done))
+    return tree_from_set(leaves, cx, cy, side)
+
+
+def tree_from_set(leaves, cx, cy, side) -> Tree:
+    arr = np.array(sorted(leaves), dtype=np.int64)
+    return Tree(cx, cy, side, arr[:, 0].astype(np.int32), arr[:, 1].astype(np.int32),
+                arr[:, 2].astype(np.int32))
+
+
+def random_balanced_tree(rng: np.random.Generator, n_splits: int, max_depth: int,
+                         cx=0.0, cy=0.0, side=2.0, min_depth=1) -> Tree:
+    """A randomly refined, 2:1-balanced tree (for list and parity tests)."""
+    leaves = {(min_depth, x, y) for y in range(1 << min_depth) for x in range(1 << min_depth)}
+    for _ in range(n_splits):
+        cand = [b for b in leaves if b[0] < max_depth]
+        if not cand:
+            break
+        b = cand[rng.integers(len(cand))]
+        leaves.discard(b)
+        leaves.update(_children(*b))
+        leaves = balance_21(leaves)
+    return tree_from_set(leaves, cx, cy, side)
+
+
+# --------------------------------------------------------------------------
+# sources
+
+def gaussian_sum(centers, widths, amps):
+    """f(x) = sum_k a_k exp(-|x - c_k|^2 / w_k^2)  (width read as in exp(-r^2/w^2))."""
+    centers = np.asarray(centers, np.float64)
+    widths = np.asarray(widths, np.float64)
+    amps = np.asarray(amps, np.float64)
+
+    def fn(X, Y):
+        out = np.zeros(np.broadcast(X, Y).shape)
+        for (c, w, a) in zip(centers, widths, amps):
+            out = out + a * np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2) / (w * w))
+        return out
+    return fn
+
+
+def smooth_step(s):
+    """C-infinity step: 1 for s <= 0, 0 for s >= 1, built from exp(-1/t)."""
+    s = np.asarray(s, np.float64)
+    a = np.clip(1.0 - s, 0.0, 1.0)
+    b = np.clip(s, 0.0, 1.0)
+    with np.errstate(divide="ignore"):
+        pa = np.where(a > 0, np.exp(-1.0 / np.where(a > 0, a, 1.0)), 0.0)
+        pb = np.where(b > 0, np.exp(-1.0 / np.where(b > 0, b, 1.0)), 0.0)
+    return pa / (pa + pb)
+
+
+def star_source(rng: np.random.Generator, n_gauss=20, blend=0.05, amp_star=0.3, k_star=5):
+    """Smooth field inside r(t) = 1 + 0.3 cos(5t + phi), blended to zero outside
+    over a radial band of width ``blend``, plus narrow seeded Gaussians inside."""
+    phi = rng.uniform(0.0, 2 * np.pi)
+    th = rng.uniform(0.0, 2 * np.pi, n_gauss)
+    frac = np.sqrt(rng.uniform(0.0, 1.0, n_gauss)) * 0.8
+    rr = frac * (1.0 + amp_star * np.cos(k_star * th + phi))
+    centers = np.stack([rr * np.cos(th), rr * np.sin(th)], axis=1)
+    widths = rng.uniform(0.01, 0.05, n_gauss)
+    amps = rng.uniform(-1.0, 1.0, n_gauss)
+    gs = gaussian_sum(centers, widths, amps)
+
+    def fn(X, Y):
+        r = np.hypot(X, Y)
+        t = np.arctan2(Y, X)
+        rb = 1.0 + amp_star * np.cos(k_star * t + phi)
+        chi = smooth_step((r - rb) / blend)
+        return chi * (np.cos(2 * X) * np.sin(3 * Y) + 0.5 + gs(X, Y))
+    return fn
+
+
+# --------------------------------------------------------------------------
+# the workloads
+
+def small_gaussian_workload(seed=1, depth=3, p=8, alpha=10.0, kernel=KERNEL_MHELMHOLTZ,
+                            n_gauss=3, side=2.0) -> Workload:
+    """Box [-1,1]^2, uniform depth-3 tree (64 leaves), p=8 (4096 nodes), alpha=10,
+    f = sum of 3 Gaussians with centres U[-0.5,0.5]^2, widths U[0.1,0.3], amplitudes U[-1,1]."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-0.5, 0.5, (n_gauss, 2))
+    w = rng.uniform(0.1, 0.3, n_gauss)
+    a = rng.uniform(-1.0, 1.0, n_gauss)
+    fn = gaussian_sum(c, w, a)
+    tree = uniform_tree(depth, side=side)
+    X, Y = node_coords(tree, p)
+    return Workload(f"gauss3_uniform_d{depth}_p{p}_a{alpha:g}", kernel, alpha, p, tree, fn(X, Y), fn)
+
+
+def star_adaptive_workload(seed=2, alpha=300.0, p=16, tol=1e-11, max_depth=10, n_gauss=20,
+                           kernel=KERNEL_MBIHARMONIC, side=3.0) -> Workload:
+    """Box [-1.5,1.5]^2, modified-biharmonic kernel, p=16, tree refined until the
+    leaf Legendre tail is below tol (max depth 10), source = star blend + 20 Gaussians."""
+    rng = np.random.default_rng(seed)
+    fn = star_source(rng, n_gauss=n_gauss)
+    tree = adaptive_tree(fn, p, 0.0, 0.0, side, tol, max_depth, min_depth=2)
+    X, Y = node_coords(tree, p)
+    return Workload(f"star_adaptive_p{p}_a{alpha:g}", kernel, alpha, p, tree, fn(X, Y), fn)
+
+
+def batched_workloads(seed=4, n_trees=64, nmin=1e4, nmax=5e5, amin=10.0, amax=1000.0,
+                      p_choices=(8, 12, 16), side=2.0):
+    """64 independent trees: node counts log-uniform in [1e4, 5e5], alpha log-uniform
+    in [10, 1000], p from {8, 12, 16}, 3-10 seeded Gaussians each; leaves are refined
+    around the Gaussian centres until the node count reaches its target, then balanced."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_trees):
+        target = float(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+        alpha = float(np.exp(rng.uniform(np.log(amin), np.log(amax))))
+        p = int(rng.choice(p_choices))
+        ng = int(rng.integers(3, 11))
+        c = rng.uniform(-0.6, 0.6, (ng, 2))
+        w = rng.uniform(0.02, 0.2, ng)
+        a = rng.uniform(-1.0, 1.0, ng)
+        fn = gaussian_sum(c, w, a)
+        leaves = {(2, x, y) for y in range(4) for x in range(4)}
+        n_target_leaves = max(16, int(target / (p * p)))
+        while len(leaves) < n_target_leaves:
+            # split the leaves nearest to any centre, largest first
+            arr = np.array(sorted(leaves), dtype=np.int64)
+            h = side / (2.0 ** arr[:, 0])
+            xc = -side / 2 + (arr[:, 1] + 0.5) * h
+            yc = -side / 2 + (arr[:, 2] + 0.5) * h
+            d = np.min(np.hypot(xc[:, None] - c[None, :, 0], yc[:, None] - c[None, :, 1]) / w[None, :], axis=1)
+            score = h / (1.0 + d)
+            order = np.argsort(-score)
+            n_split = max(1, min(len(order), (n_target_leaves - len(leaves)) // 3 + 1))
+            for idx in order[:n_split]:
+                b = tuple(int(v) for v in arr[idx])
+                if b[0] >= 12:
+                    continue
+                leaves.discard(b)
+                leaves.update(_children(*b))
+            leaves = balance_21(leaves)
+        tree = tree_from_set(leaves, 0.0, 0.0, side)
+        X, Y = node_coords(tree, p)
+        out.append(Workload(f"batch{k}_p{p}_a{alpha:.1f}", KERNEL_MHELMHOLTZ, alpha, p, tree, fn(X, Y), fn))
+    return out
