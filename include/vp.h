@@ -1,0 +1,201 @@
+/*
+ * vp.h -- C ABI of the GB300 volume-potential library (libvp.so).
+ *
+ * The library evaluates the free-space volume potential of a source sampled on
+ * the leaves of a level-restricted quadtree (af Klinteberg, Askham & Kropinski,
+ * "A fast integral equation method for the two-dimensional Navier-Stokes
+ * equations", Sec. 2.1, Eq. vol_pot, in its scalar form):
+ *
+ *     u(x) = sum over leaves L of int_L G(x - y) f_L(y) dy,   and grad u(x),
+ *
+ * at every leaf node x, where f_L is the tensor Lagrange interpolant of the
+ * nodal values of the leaf and G is one of
+ *
+ *     VP_KERNEL_MHELMHOLTZ   G1(r) = K0(alpha r) / (2 pi)
+ *                            (free-space Green's function of alpha^2 - Laplacian,
+ *                            the elliptic operator each implicit time step of
+ *                            Sec. 2 reduces to);
+ *     VP_KERNEL_MBIHARMONIC  G2(r) = (K0(alpha r) + log r) / (2 pi alpha^2)
+ *                            = Q0(r) / (2 pi alpha^2) with Q0 of Sec. 3.2.1 (Eq. Q0);
+ *                            minus the modified-biharmonic Green's function of
+ *                            Sec. 2 (Eq. modbiharm), i.e. Laplacian(alpha^2 -
+ *                            Laplacian) G2 = delta.
+ *
+ * Method: adjacent leaves interact through precomputed per-level leaf-to-leaf
+ * tables (one dense matrix per relative position); well-separated interactions
+ * go through a fast multipole method with expansions in K_n / I_n (and, for
+ * G2, the log / r^n Laplace part), following the separation-of-variables
+ * representations of Sec. 3.2.1 (Eqs. mpole, loc) on the level-restricted tree
+ * of Sec. 3.2.1 ("Tree structure").
+ *
+ * Conventions shared by every entry point:
+ *  - Root box: centre (cx, cy), side `root_side`. A leaf is (level, ix, iy):
+ *    side h = root_side / 2^level, lower-left corner
+ *    (cx - root_side/2 + ix*h, cy - root_side/2 + iy*h), 0 <= ix, iy < 2^level.
+ *  - Each leaf carries p x p Gauss-Legendre nodes (tensor product of the
+ *    p-point Gauss-Legendre rule mapped to the leaf); node (i, j), i the x
+ *    index, has index j*p + i within its leaf; leaves are stored in the order
+ *    given to vp_tree_upload. N = n_leaves * p * p.
+ *  - Device pointers are plain CUDA device addresses owned by the caller
+ *    (for example torch tensors' data_ptr()); handles are owned by the library.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). Every call
+ *    that takes a stream is asynchronous on it unless stated otherwise.
+ *  - Every function returns VP_OK (0) or a negative VP_ERR_* code; nothing
+ *    throws across the ABI. vp_strerror() names a code.
+ */
+#ifndef VP_H_
+#define VP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vp_tables_s* vp_tables;
+typedef struct vp_tree_s* vp_tree;
+
+enum { VP_KERNEL_MHELMHOLTZ = 0, VP_KERNEL_MBIHARMONIC = 1 };
+enum { VP_PREC_FP64 = 0, VP_PREC_SPLIT = 1 };
+
+enum {
+  VP_OK = 0,
+  VP_ERR_ARG = -1,             /* an argument is out of range or NULL */
+  VP_ERR_TREE_UNBALANCED = -2, /* adjacent leaves differ by more than one level */
+  VP_ERR_LEVELS = -3,          /* a leaf is deeper than the tables were built for */
+  VP_ERR_OOM = -4,             /* a device or host allocation failed */
+  VP_ERR_CUDA = -5,            /* a CUDA runtime call failed */
+  VP_ERR_TREE = -6,            /* leaves overlap, leave gaps, or lie outside the root */
+  VP_ERR_TIMEOUT = -7          /* a bounded device wait ran out */
+};
+
+/*
+ * vp_tables_build -- precompute every per-level operator for one kernel.
+ *
+ * Builds, on the device, for levels 0..levels (leaf side root_side/2^level):
+ *  - the leaf-to-leaf near tables: for each of the 33 relative positions of
+ *    an adjacent leaf (self, 8 same-level neighbours, 12 coarser and 12
+ *    finer adjacent leaves) a dense [3 p^2 x p^2] matrix mapping the source
+ *    leaf's nodal values to u, du/dx, du/dy at the target leaf's nodes
+ *    (integrals of the kernel against the Lagrange basis, Eq. vol_pot);
+ *  - the expansion operators of order `order` (the truncation P of Eqs.
+ *    mpole/loc; 2P+1 real coefficients per channel): source-to-multipole,
+ *    multipole-to-multipole, multipole-to-local (40 offsets), local-to-local,
+ *    local-to-target (values and gradients), multipole-to-target and
+ *    source-to-local for the adaptive W and X lists.
+ *  kernel     VP_KERNEL_MHELMHOLTZ or VP_KERNEL_MBIHARMONIC.
+ *  alpha      > 0.
+ *  p          nodes per leaf side, 2 <= p <= 16.
+ *  levels     deepest leaf level the tables serve, 0 <= levels <= 20.
+ *  root_side  side of the root box (> 0); the tables depend on absolute leaf
+ *             sizes because K0(alpha r) is not scale invariant.
+ *  order      expansion order P, 4 <= P <= 60 (40 gives about 12 digits, as in
+ *             Sec. 3.2.1).
+ *  precision  VP_PREC_FP64 (all contractions in FP64) or VP_PREC_SPLIT (the
+ *             near-table contraction on tensor cores with sliced operands).
+ *  stream     stream for the build kernels; the call synchronises it before
+ *             returning.
+ *  out        receives the handle; free with vp_tables_free.
+ * Errors: VP_ERR_ARG, VP_ERR_OOM, VP_ERR_CUDA.
+ */
+int vp_tables_build(int kernel, double alpha, int p, int levels, double root_side, int order,
+                    int precision, void* stream, vp_tables* out);
+
+/*
+ * vp_tree_upload -- validate a leaf list and build its interaction lists.
+ *
+ * Checks that the leaves tile the root box exactly (no overlap, no gap) and
+ * that adjacent leaves differ by at most one level (the level restriction of
+ * Sec. 3.2.1), builds the adaptive FMM lists (U: adjacent leaves; V: same-level
+ * well-separated boxes; W/X: the mixed-level lists), groups every interaction
+ * by operator, and uploads the work descriptors to the device.
+ *  tables   built by vp_tables_build; must outlive the tree.
+ *  cx, cy   root box centre (its side is the tables' root_side).
+ *  level, ix, iy  HOST arrays of n_leaves entries (n_leaves >= 1).
+ *  stream   stream for the uploads; the call synchronises it before returning.
+ * Errors: VP_ERR_ARG, VP_ERR_TREE, VP_ERR_TREE_UNBALANCED, VP_ERR_LEVELS,
+ * VP_ERR_OOM, VP_ERR_CUDA.
+ */
+int vp_tree_upload(vp_tables tables, double cx, double cy, int n_leaves, const int32_t* level,
+                   const int32_t* ix, const int32_t* iy, void* stream, vp_tree* out);
+
+/* Number of leaves and nodes (N = n_leaves * p^2) of a tree. */
+int vp_tree_size(vp_tree tree, int64_t* n_leaves, int64_t* n_nodes);
+
+/*
+ * vp_tree_nodes -- node coordinates of the tree, computed on the device.
+ *  xy  device array [2][N]: xy[0..N) = x, xy[N..2N) = y, in node order.
+ */
+int vp_tree_nodes(vp_tree tree, double* xy, void* stream);
+
+/*
+ * vp_eval -- the volume potential and its gradient at every node.
+ *  f      device [N] nodal source values (read only).
+ *  u      device [N] output.
+ *  gradu  device [2][N] output: du/dx then du/dy.
+ * Outputs are overwritten. The tree's work buffers are reused, so calls on
+ * one tree must not overlap on the GPU (issue them on one stream).
+ * Errors: VP_ERR_ARG, VP_ERR_CUDA (launch failures are reported; asynchronous
+ * faults surface at the next synchronising call).
+ */
+int vp_eval(vp_tree tree, const double* f, double* u, double* gradu, void* stream);
+
+/*
+ * vp_eval_host -- vp_eval from and to HOST memory.
+ *  f (host [N]) is copied to the device, the potential is evaluated, and u
+ *  (host [N]) and gradu (host [2][N]) are copied back; the call synchronises
+ *  `stream` before returning. Pinned host memory makes the copies faster.
+ *  Device staging buffers are owned by the tree (allocated on first use).
+ */
+int vp_eval_host(vp_tree tree, const double* f, double* u, double* gradu, void* stream);
+
+/* Stages of one evaluation, for vp_eval_timed and vp_tree_stats. */
+enum {
+  VP_STAGE_UPWARD = 0,   /* clear, source-to-multipole, multipole-to-multipole */
+  VP_STAGE_M2L = 1,      /* multipole-to-local (V lists), source-to-local (X lists) */
+  VP_STAGE_DOWNWARD = 2, /* local reduction, local-to-local */
+  VP_STAGE_TARGETS = 3,  /* local-to-target, multipole-to-target (W lists) */
+  VP_STAGE_NEAR = 4,     /* near tables (U lists) */
+  VP_STAGE_OUTPUT = 5,   /* reduction into u and grad u */
+  VP_NSTAGES = 6
+};
+
+/*
+ * vp_eval_timed -- vp_eval with a CUDA event recorded on `stream` between
+ * stages; waits for the last event and writes the milliseconds of each stage
+ * to stage_ms[VP_NSTAGES] (host array). Same arguments and errors as vp_eval.
+ */
+int vp_eval_timed(vp_tree tree, const double* f, double* u, double* gradu, void* stream, float* stage_ms);
+
+/*
+ * vp_tree_stats -- static work of one evaluation of `tree`:
+ *  launches     number of kernel launches (and memsets) one vp_eval issues;
+ *  stage_flops  host array [VP_NSTAGES]: algorithmic floating-point operations
+ *               per stage (2*M*K per column of each contraction, one add per
+ *               reduced element). Either pointer may be NULL.
+ */
+int vp_tree_stats(vp_tree tree, int64_t* launches, double* stage_flops);
+
+/*
+ * vp_plan_pairs -- host-only planning diagnostic (no GPU needed): validates a
+ * leaf list like vp_tree_upload and returns, for every interaction the lists
+ * generate, the covered (target leaf, source leaf) pairs with the mechanism
+ * (0 near table, 1 multipole-to-local, 2 multipole-to-target, 3
+ * source-to-local). Call with tgt = src = mech = NULL to get the count in
+ * *n_out, then with arrays of that size. Errors as vp_tree_upload.
+ */
+int vp_plan_pairs(int n_leaves, const int32_t* level, const int32_t* ix, const int32_t* iy, int64_t* n_out,
+                  int32_t* tgt, int32_t* src, int32_t* mech);
+
+/* Free a tree (after work on it has finished) / tables (after their trees). */
+void vp_tree_free(vp_tree tree);
+void vp_tables_free(vp_tables tables);
+
+/* Static description of an error code. */
+const char* vp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VP_H_ */

@@ -309,8 +309,8 @@ int ora_volume_potential(int kernel, double alpha, int p, double cx, double cy, 
   }
   int status = 0;
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 1)
+  const int nt = nthreads > 0 ? nthreads : omp_get_num_procs();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
 #endif
   for (int t = 0; t < n_targets; ++t) {
     Acc acc;
@@ -330,7 +330,7 @@ int ora_volume_potential(int kernel, double alpha, int p, double cx, double cy, 
 
 int ora_num_threads(void) {
 #ifdef _OPENMP
-  return omp_get_max_threads();
+  return omp_get_num_procs();
 #else
   return 1;
 #endif

@@ -1,0 +1,230 @@
+"""GB300 volume-potential library: thin Python binding of libvp.so.
+
+The functions below carry the names of the C ABI in ``include/vp.h`` and only
+marshal arguments (PyTorch supplies device memory and streams). Every step of
+the computation runs in the library's CUDA kernels; there is no Python or CPU
+fallback: if the compiled library is missing, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded input generators, no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvp.so")
+
+VP_KERNEL_MHELMHOLTZ = 0
+VP_KERNEL_MBIHARMONIC = 1
+VP_PREC_FP64 = 0
+VP_PREC_SPLIT = 1
+
+_lib = None
+
+
+class VPError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {vp_strerror(code)} ({code})" if what else f"{vp_strerror(code)} ({code})")
+
+
+def load_library():
+    """Load libvp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libvp.so not built at {LIB_PATH}; run paper_1908_07392_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    lib.vp_tables_build.argtypes = [c_int, c_double, c_int, c_int, c_double, c_int, c_int, c_void_p,
+                                    ctypes.POINTER(c_void_p)]
+    lib.vp_tree_upload.argtypes = [c_void_p, c_double, c_double, c_int, i32p, i32p, i32p, c_void_p,
+                                   ctypes.POINTER(c_void_p)]
+    lib.vp_tree_size.argtypes = [c_void_p, i64p, i64p]
+    lib.vp_tree_nodes.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.vp_eval.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.vp_eval_host.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.vp_tree_free.argtypes = [c_void_p]
+    lib.vp_tree_free.restype = None
+    lib.vp_tables_free.argtypes = [c_void_p]
+    lib.vp_tables_free.restype = None
+    lib.vp_strerror.argtypes = [c_int]
+    lib.vp_strerror.restype = ctypes.c_char_p
+    lib.vp_plan_pairs.argtypes = [c_int, i32p, i32p, i32p, i64p, i32p, i32p, i32p]
+    lib.vp_eval_timed.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(ctypes.c_float)]
+    lib.vp_tree_stats.argtypes = [c_void_p, i64p, ctypes.POINTER(c_double)]
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names declared in include/vp.h (the ABI surface)."""
+    return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_eval", "vp_eval_host",
+            "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs"]
+
+
+VP_NSTAGES = 6
+STAGE_NAMES = ["upward", "m2l", "downward", "targets", "near", "output"]
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise VPError(rc, what)
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def vp_strerror(code: int) -> str:
+    return load_library().vp_strerror(int(code)).decode()
+
+
+def vp_tables_build(kernel: int, alpha: float, p: int, levels: int, root_side: float, order: int = 40,
+                    precision: int = VP_PREC_FP64, stream=None) -> int:
+    out = ctypes.c_void_p()
+    rc = load_library().vp_tables_build(int(kernel), float(alpha), int(p), int(levels), float(root_side),
+                                        int(order), int(precision), _stream_ptr(stream), ctypes.byref(out))
+    _check(rc, "vp_tables_build")
+    return out.value
+
+
+def vp_tree_upload(tables: int, cx: float, cy: float, level, ix, iy, stream=None) -> int:
+    lv, plv = _i32(level)
+    xx, pix = _i32(ix)
+    yy, piy = _i32(iy)
+    out = ctypes.c_void_p()
+    rc = load_library().vp_tree_upload(ctypes.c_void_p(tables), float(cx), float(cy), int(lv.size), plv, pix, piy,
+                                       _stream_ptr(stream), ctypes.byref(out))
+    _check(rc, "vp_tree_upload")
+    return out.value
+
+
+def vp_tree_size(tree: int):
+    a = ctypes.c_int64(); b = ctypes.c_int64()
+    _check(load_library().vp_tree_size(ctypes.c_void_p(tree), ctypes.byref(a), ctypes.byref(b)), "vp_tree_size")
+    return a.value, b.value
+
+
+def vp_tree_nodes(tree: int, xy, stream=None):
+    _check(load_library().vp_tree_nodes(ctypes.c_void_p(tree), ctypes.c_void_p(xy.data_ptr()), _stream_ptr(stream)),
+           "vp_tree_nodes")
+
+
+def vp_eval(tree: int, f, u, gradu, stream=None):
+    """f, u: device float64 [N]; gradu: device float64 [2, N] (torch tensors, contiguous)."""
+    for t in (f, u, gradu):
+        if not (t.is_cuda and t.is_contiguous()) or str(t.dtype) != "torch.float64":
+            raise ValueError("vp_eval expects contiguous float64 CUDA tensors")
+    _check(load_library().vp_eval(ctypes.c_void_p(tree), ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                  ctypes.c_void_p(gradu.data_ptr()), _stream_ptr(stream)), "vp_eval")
+
+
+def vp_eval_timed(tree: int, f, u, gradu, stream=None):
+    """vp_eval with CUDA events between stages; returns milliseconds per stage (list of VP_NSTAGES)."""
+    ms = (ctypes.c_float * VP_NSTAGES)()
+    _check(load_library().vp_eval_timed(ctypes.c_void_p(tree), ctypes.c_void_p(f.data_ptr()),
+                                        ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(gradu.data_ptr()),
+                                        _stream_ptr(stream), ms), "vp_eval_timed")
+    return list(ms)
+
+
+def vp_tree_stats(tree: int):
+    """(launches per evaluation, algorithmic flops per stage)."""
+    n = ctypes.c_int64()
+    fl = (ctypes.c_double * VP_NSTAGES)()
+    _check(load_library().vp_tree_stats(ctypes.c_void_p(tree), ctypes.byref(n), fl), "vp_tree_stats")
+    return n.value, list(fl)
+
+
+def vp_eval_host(tree: int, f, u, gradu, stream=None):
+    """f, u: host float64 [N]; gradu: host float64 [2, N] (numpy arrays or CPU tensors, contiguous)."""
+    def ptr(a):
+        return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+    _check(load_library().vp_eval_host(ctypes.c_void_p(tree), ptr(f), ptr(u), ptr(gradu), _stream_ptr(stream)),
+           "vp_eval_host")
+
+
+def vp_tree_free(tree: int):
+    if tree:
+        load_library().vp_tree_free(ctypes.c_void_p(tree))
+
+
+def vp_tables_free(tables: int):
+    if tables:
+        load_library().vp_tables_free(ctypes.c_void_p(tables))
+
+
+def vp_plan_pairs(level, ix, iy):
+    """Host-only: (target leaf, source leaf, mechanism) triples covered by the interaction lists
+    (mechanism 0 = near table, 1 = multipole-to-local, 2 = multipole-to-target, 3 = source-to-local)."""
+    lib = load_library()
+    lv, plv = _i32(level)
+    xx, pix = _i32(ix)
+    yy, piy = _i32(iy)
+    n = ctypes.c_int64()
+    _check(lib.vp_plan_pairs(int(lv.size), plv, pix, piy, ctypes.byref(n), None, None, None), "vp_plan_pairs")
+    t = np.zeros(n.value, np.int32); s = np.zeros(n.value, np.int32); m = np.zeros(n.value, np.int32)
+    _check(lib.vp_plan_pairs(int(lv.size), plv, pix, piy, ctypes.byref(n), _i32(t)[1], _i32(s)[1], _i32(m)[1]),
+           "vp_plan_pairs")
+    return t, s, m
+
+
+class VolumePotential:
+    """Tables + tree for one workload; evaluates u and grad u at every leaf node on the GPU."""
+
+    def __init__(self, kernel, alpha, p, tree, order=40, precision=VP_PREC_FP64, levels=None, stream=None):
+        import torch
+        self.p = p
+        self.levels = int(tree.max_level if levels is None else levels)
+        self.tables = vp_tables_build(kernel, alpha, p, self.levels, tree.side, order, precision, stream)
+        try:
+            self.tree = vp_tree_upload(self.tables, tree.cx, tree.cy, tree.level, tree.ix, tree.iy, stream)
+        except Exception:
+            vp_tables_free(self.tables)
+            raise
+        self.n_leaves, self.N = vp_tree_size(self.tree)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def nodes(self):
+        import torch
+        xy = torch.empty(2, self.N, dtype=torch.float64, device=self.device)
+        vp_tree_nodes(self.tree, xy)
+        return xy
+
+    def __call__(self, f, u=None, gradu=None):
+        import torch
+        if u is None:
+            u = torch.empty(self.N, dtype=torch.float64, device=f.device)
+        if gradu is None:
+            gradu = torch.empty(2, self.N, dtype=torch.float64, device=f.device)
+        vp_eval(self.tree, f, u, gradu)
+        return u, gradu
+
+    def close(self):
+        if getattr(self, "tree", None):
+            vp_tree_free(self.tree)
+            self.tree = None
+        if getattr(self, "tables", None):
+            vp_tables_free(self.tables)
+            self.tables = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,644 @@
+// Evaluation engine: vp_tree_upload, vp_eval, vp_eval_host and friends.
+//
+// Every step of the volume potential is a set of small dense contractions
+// y_dst (=|+=) A_op x_src, where A_op is a precomputed operator chosen by
+// (level, relative position) and x_src / y_dst are per-box vectors (nodal
+// values, multipole or local coefficients). The planner groups the
+// contractions by operator so that each group is one GEMM whose columns are
+// gathered from (and scattered to) arbitrary vectors; several destinations
+// that receive more than one contribution get private scratch slots that a
+// deterministic segmented reduction sums in a fixed order afterwards.
+//
+// Pass order (one stream):
+//   S2M (leaves) -> M2M (deepest parent level first) -> M2L (V lists) and
+//   S2L (X lists) into local slots -> reduce into local expansions ->
+//   L2L (coarsest first) -> L2T, M2T (W lists) and near tables (U lists) into
+//   output slots -> reduce into u, du/dx, du/dy.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <vector>
+
+#include "plan.h"
+#include "vp_internal.h"
+
+namespace vp {
+
+enum Buf { BUF_F = 0, BUF_MP, BUF_LOC, BUF_LSLOT, BUF_USLOT, BUF_COUNT };
+
+struct Tile {
+  int group, m0, col0, ncol;
+};
+
+struct GemmArgs {
+  int M, K, kseg, lda, accumulate;
+  long long seg_stride;
+  const double* A;
+  const double* X;
+  double* Y;
+  const Tile* tiles;
+  const long long* a_off;
+  const long long* src_off;
+  const long long* dst_off;
+};
+
+// FP64 gather-GEMM: tile (64 rows x 64 columns), K in steps of 16, 256 threads,
+// each thread 4 rows (strided by 16) x 4 columns; rows of a destination vector
+// are contiguous, so a half-warp stores 16 consecutive doubles.
+constexpr int kBM = 64, kBN = 64, kBK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_gather_f64(GemmArgs a) {
+  __shared__ double As[kBK][kBM + 2];
+  __shared__ double Bs[kBK][kBN + 2];
+  const Tile tile = a.tiles[blockIdx.x];
+  const double* __restrict__ A = a.A + a.a_off[tile.group];
+  const int tid = threadIdx.x;
+  const int tr = tid & 15;   // row lane
+  const int tc = tid >> 4;   // column group (0..15)
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = 0; k0 < a.K; k0 += kBK) {
+    // A tile: 64 rows x 16 k
+    for (int e = tid; e < kBM * kBK; e += 256) {
+      const int r = e / kBK, kk = e % kBK;
+      const int gm = tile.m0 + r, gk = k0 + kk;
+      As[kk][r] = (gm < a.M && gk < a.K) ? A[(size_t)gm * a.lda + gk] : 0.0;
+    }
+    // B tile: 16 k x 64 columns, gathered
+    for (int e = tid; e < kBN * kBK; e += 256) {
+      const int c = e / kBK, kk = e % kBK;
+      const int gk = k0 + kk;
+      double v = 0.0;
+      if (c < tile.ncol && gk < a.K) {
+        const long long base = a.src_off[tile.col0 + c];
+        const int sg = gk / a.kseg, si = gk - sg * a.kseg;
+        v = a.X[base + sg * a.seg_stride + si];
+      }
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][tr + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tc * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = tc * 4 + j;
+    if (c >= tile.ncol) continue;
+    double* __restrict__ y = a.Y + a.dst_off[tile.col0 + c];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = tile.m0 + tr + 16 * i;
+      if (r < a.M) y[r] = a.accumulate ? y[r] + acc[i][j] : acc[i][j];
+    }
+  }
+}
+
+struct ReduceArgs {
+  int M, n;               // vector length; nodes per leaf (final output)
+  int final_out;          // 1: write u / gradu layout
+  long long N;            // nodes (final output)
+  const long long* dst_off;
+  const long long* ptr;   // CSR over destinations
+  const long long* slot;  // scratch offsets
+  const double* S;        // scratch base
+  double* Y;              // destination base (non-final)
+  double* u;              // final: u [N]
+  double* g;              // final: gradu [2][N]
+};
+
+__global__ void k_reduce(ReduceArgs a) {
+  const int d = blockIdx.x;
+  const long long b = a.ptr[d], e = a.ptr[d + 1];
+  for (int r = threadIdx.x; r < a.M; r += blockDim.x) {
+    double s = 0.0;
+    for (long long k = b; k < e; ++k) s += a.S[a.slot[k] + r];
+    if (a.final_out) {
+      const int f = r / a.n, t = r - f * a.n;
+      const long long o = a.dst_off[d] + t;  // leaf * n + t
+      if (f == 0) a.u[o] = s;
+      else a.g[(f - 1) * a.N + o] = s;
+    } else {
+      a.Y[a.dst_off[d] + r] = s;
+    }
+  }
+}
+
+__global__ void k_nodes(int p, int n_leaves, double x0, double y0, double side, const int* lv, const int* ix,
+                        const int* iy, const double* xi, long long N, double* xy) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int n = p * p;
+  const long long leaf = i / n;
+  const int t = (int)(i - leaf * n);
+  const double h = side / (double)(1ll << lv[leaf]);
+  xy[i] = x0 + (ix[leaf] + 0.5 * (1.0 + xi[t % p])) * h;
+  xy[N + i] = y0 + (iy[leaf] + 0.5 * (1.0 + xi[t / p])) * h;
+}
+
+// ----------------------------------------------------------------- host plan -> device ops
+
+struct HostGemm {
+  int M = 0, K = 0, kseg = 0, lda = 0, accumulate = 0;
+  long long seg_stride = 0;
+  int table = 0;  // which table array
+  int src = 0, dst = 0;
+  struct Entry { long long a, s, d; };
+  std::vector<Entry> entries;
+};
+
+struct DevGemm {
+  GemmArgs args;
+  int src, dst, table;
+  int n_tiles;
+};
+
+struct HostReduce {
+  int M = 0, final_out = 0, dst = 0, src = 0;
+  std::vector<long long> dst_off, ptr, slot;
+};
+
+struct DevReduce {
+  ReduceArgs args;
+  int dst, src, n_dst;
+};
+
+enum Table { T_NEAR, T_S2M, T_L2T, T_M2M, T_L2L, T_M2L, T_M2T, T_S2L, T_SPLIT };
+
+struct Step {
+  int kind;   // 0 gemm, 1 reduce, 2 memset mp, 3 split-precision near (split.cu)
+  int index;
+  int stage;  // VP_STAGE_* for timing
+};
+
+}  // namespace vp
+
+struct vp_tree_s {
+  vp_tables_s* T = nullptr;
+  int n_leaves = 0, n_boxes = 0, max_level = 0;
+  long long N = 0;
+  double cx = 0.0, cy = 0.0;
+  // device
+  int *d_lv = nullptr, *d_ix = nullptr, *d_iy = nullptr;
+  double* d_xi = nullptr;
+  double *mp = nullptr, *loc = nullptr, *lslot = nullptr, *uslot = nullptr;
+  long long n_lslot = 0, n_uslot = 0;
+  std::vector<void*> allocs;  // every device allocation owned by the tree
+  std::vector<vp::DevGemm> gemms;
+  std::vector<vp::DevReduce> reduces;
+  std::vector<vp::Step> steps;
+  int cur_stage = 0;        // stage tag given to steps as they are planned
+  double flops[VP_NSTAGES] = {0};
+  // split-precision near pass (if the tables are VP_PREC_SPLIT)
+  void* split_plan = nullptr;
+  // host staging for vp_eval_host
+  double *h_f = nullptr, *h_u = nullptr;
+  double *d_f = nullptr, *d_u = nullptr, *d_g = nullptr;
+};
+
+namespace vp {
+namespace {
+
+#define TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_last_cuda(e_); return e_ == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA; } } while (0)
+
+template <class T>
+int dev_upload(vp_tree_s* tr, const std::vector<T>& v, T** out, cudaStream_t s) {
+  *out = nullptr;
+  if (v.empty()) return VP_OK;
+  void* p = nullptr;
+  TRY(cudaMalloc(&p, v.size() * sizeof(T)));
+  tr->allocs.push_back(p);
+  TRY(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  *out = static_cast<T*>(p);
+  return VP_OK;
+}
+
+int upload_gemm(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
+  if (g.entries.empty()) return VP_OK;
+  std::stable_sort(g.entries.begin(), g.entries.end(),
+                   [](const HostGemm::Entry& x, const HostGemm::Entry& y) { return x.a < y.a; });
+  std::vector<long long> a_off, src_off, dst_off;
+  std::vector<Tile> tiles;
+  size_t i = 0;
+  while (i < g.entries.size()) {
+    size_t j = i;
+    while (j < g.entries.size() && g.entries[j].a == g.entries[i].a) ++j;
+    const int grp = (int)a_off.size();
+    a_off.push_back(g.entries[i].a);
+    const int col_begin = (int)src_off.size();
+    for (size_t k = i; k < j; ++k) { src_off.push_back(g.entries[k].s); dst_off.push_back(g.entries[k].d); }
+    const int ncols = (int)(j - i);
+    for (int m0 = 0; m0 < g.M; m0 += kBM)
+      for (int c0 = 0; c0 < ncols; c0 += kBN) tiles.push_back({grp, m0, col_begin + c0, std::min(kBN, ncols - c0)});
+    i = j;
+  }
+  DevGemm d{};
+  d.args.M = g.M; d.args.K = g.K; d.args.kseg = g.kseg ? g.kseg : g.K; d.args.lda = g.lda;
+  d.args.accumulate = g.accumulate; d.args.seg_stride = g.seg_stride;
+  Tile* dt; long long *da, *ds, *dd;
+  int rc;
+  if ((rc = dev_upload(tr, tiles, &dt, s))) return rc;
+  if ((rc = dev_upload(tr, a_off, &da, s))) return rc;
+  if ((rc = dev_upload(tr, src_off, &ds, s))) return rc;
+  if ((rc = dev_upload(tr, dst_off, &dd, s))) return rc;
+  d.args.tiles = dt; d.args.a_off = da; d.args.src_off = ds; d.args.dst_off = dd;
+  d.src = g.src; d.dst = g.dst; d.table = g.table; d.n_tiles = (int)tiles.size();
+  tr->steps.push_back({0, (int)tr->gemms.size(), tr->cur_stage});
+  tr->gemms.push_back(d);
+  tr->flops[tr->cur_stage] += 2.0 * g.M * (double)g.K * (double)g.entries.size();
+  return VP_OK;
+}
+
+int upload_reduce(vp_tree_s* tr, HostReduce& r, cudaStream_t s) {
+  if (r.dst_off.empty()) return VP_OK;
+  DevReduce d{};
+  d.args.M = r.M; d.args.n = tr->T->n; d.args.final_out = r.final_out; d.args.N = tr->N;
+  long long *a, *b, *c;
+  int rc;
+  if ((rc = dev_upload(tr, r.dst_off, &a, s))) return rc;
+  if ((rc = dev_upload(tr, r.ptr, &b, s))) return rc;
+  if ((rc = dev_upload(tr, r.slot, &c, s))) return rc;
+  if (r.slot.empty()) {
+    // a reduction with no contributions writes zeros; give it a valid (unused) slot array
+    c = b;
+  }
+  d.args.dst_off = a; d.args.ptr = b; d.args.slot = c;
+  d.dst = r.dst; d.src = r.src; d.n_dst = (int)r.dst_off.size();
+  tr->steps.push_back({1, (int)tr->reduces.size(), tr->cur_stage});
+  tr->flops[tr->cur_stage] += (double)r.M * (double)r.slot.size();
+  tr->reduces.push_back(d);
+  return VP_OK;
+}
+
+const double* table_ptr(const vp_tables_s* T, int t) {
+  switch (t) {
+    case T_NEAR: return T->near;
+    case T_S2M: return T->s2m;
+    case T_L2T: return T->l2t;
+    case T_M2M: return T->m2m;
+    case T_L2L: return T->l2l;
+    case T_M2L: return T->m2l;
+    case T_M2T: return T->m2t;
+    case T_S2L: return T->s2l;
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+extern int split_plan_build(vp_tree_s* tr, const TreePlan& P, const std::vector<long long>& near_slot,
+                            cudaStream_t s);
+extern int split_near_run(vp_tree_s* tr, const double* f, cudaStream_t s);
+extern void split_plan_free(vp_tree_s* tr);
+extern int split_launches(const vp_tree_s* tr);
+
+int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
+  const vp_tables_s* T = tr->T;
+  const int n = T->n, C = T->C, E = T->E, nch = T->nch;
+  const auto& B = P.boxes;
+  const long long NB = (long long)B.size();
+  auto kact = [&](int l) { return l >= 0 && l <= T->levels && T->kactive[l]; };
+
+  // ---- local slots (M2L, S2L) and output slots (L2T, M2T, near)
+  std::vector<std::vector<long long>> lsl((size_t)NB * nch);
+  std::vector<std::vector<long long>> usl(B.size());
+  long long nls = 0, nus = 0;
+  HostGemm m2l, s2l, l2t, m2t, nearg, s2m;
+  m2l.M = C; m2l.K = C; m2l.lda = C; m2l.table = T_M2L; m2l.src = BUF_MP; m2l.dst = BUF_LSLOT;
+  for (const Pair& v : P.V) {
+    const int l = B[v.tgt].level;
+    for (int ch = 0; ch < nch; ++ch) {
+      if (ch == 0 && !kact(l)) continue;
+      const long long slot = nls++;
+      lsl[(size_t)v.tgt * nch + ch].push_back(slot * C);
+      m2l.entries.push_back({(long long)(l * T->m2l_stride_lvl() + v.pos * T->m2l_stride_off() + ch * T->m2l_stride_ch()),
+                             (long long)v.src * E + ch * C, slot * C});
+    }
+  }
+  s2l.M = C; s2l.K = n; s2l.lda = n; s2l.table = T_S2L; s2l.src = BUF_F; s2l.dst = BUF_LSLOT;
+  for (const Pair& x : P.X) {
+    const int l = B[x.tgt].level;
+    for (int ch = 0; ch < nch; ++ch) {
+      if (ch == 0 && !kact(l)) continue;
+      const long long slot = nls++;
+      lsl[(size_t)x.tgt * nch + ch].push_back(slot * C);
+      s2l.entries.push_back({(long long)(l * T->s2l_stride_lvl() + x.pos * T->s2l_stride_pos() + ch * T->s2l_stride_ch()),
+                             (long long)B[x.src].leaf * n, slot * C});
+    }
+  }
+  nearg.M = 3 * n; nearg.K = n; nearg.lda = n; nearg.table = T_NEAR; nearg.src = BUF_F; nearg.dst = BUF_USLOT;
+  std::vector<long long> near_slot;
+  for (const Pair& u : P.U) {
+    const int l = B[u.tgt].level;
+    const long long slot = nus++;
+    usl[u.tgt].push_back(slot * 3 * n);
+    near_slot.push_back(slot * 3 * n);
+    nearg.entries.push_back({(long long)(l * T->near_stride_lvl() + u.pos * T->near_stride_pos()),
+                             (long long)B[u.src].leaf * n, slot * 3 * n});
+  }
+  m2t.M = 3 * n; m2t.K = C; m2t.lda = C; m2t.table = T_M2T; m2t.src = BUF_MP; m2t.dst = BUF_USLOT;
+  for (const Pair& w : P.W) {
+    const int l = B[w.tgt].level;
+    for (int ch = 0; ch < nch; ++ch) {
+      if (ch == 0 && !kact(l + 1)) continue;
+      const long long slot = nus++;
+      usl[w.tgt].push_back(slot * 3 * n);
+      m2t.entries.push_back({(long long)(l * T->m2t_stride_lvl() + w.pos * T->m2t_stride_pos() + ch * T->m2t_stride_ch()),
+                             (long long)w.src * E + ch * C, slot * 3 * n});
+    }
+  }
+  l2t.M = 3 * n; l2t.K = E; l2t.lda = E; l2t.table = T_L2T; l2t.src = BUF_LOC; l2t.dst = BUF_USLOT;
+  s2m.M = E; s2m.K = n; s2m.lda = n; s2m.table = T_S2M; s2m.src = BUF_F; s2m.dst = BUF_MP;
+  for (long long i = 0; i < NB; ++i) {
+    const Box& b = B[i];
+    if (b.leaf < 0 || b.level < 2) continue;
+    const long long slot = nus++;
+    usl[i].push_back(slot * 3 * n);
+    l2t.entries.push_back({(long long)(b.level * T->l2t_stride_lvl()), i * E, slot * 3 * n});
+    s2m.entries.push_back({(long long)(b.level * T->s2m_stride_lvl()), (long long)b.leaf * n, i * E});
+  }
+  tr->n_lslot = nls;
+  tr->n_uslot = nus;
+
+  // ---- device buffers
+  TRY(cudaMalloc(&tr->mp, std::max<long long>(1, NB * E) * sizeof(double)));
+  tr->allocs.push_back(tr->mp);
+  TRY(cudaMalloc(&tr->loc, std::max<long long>(1, NB * E) * sizeof(double)));
+  tr->allocs.push_back(tr->loc);
+  TRY(cudaMalloc(&tr->lslot, std::max<long long>(1, nls * C) * sizeof(double)));
+  tr->allocs.push_back(tr->lslot);
+  TRY(cudaMalloc(&tr->uslot, std::max<long long>(1, nus * 3 * n) * sizeof(double)));
+  tr->allocs.push_back(tr->uslot);
+
+  int rc;
+  // ---- steps, in pass order
+  tr->cur_stage = VP_STAGE_UPWARD;
+  tr->steps.push_back({2, 0, tr->cur_stage});  // clear multipoles
+  if ((rc = upload_gemm(tr, s2m, s))) return rc;
+  for (int l = P.max_level - 1; l >= 2; --l) {
+    HostGemm m2m;
+    m2m.M = C; m2m.K = 4 * C; m2m.kseg = C; m2m.seg_stride = E; m2m.lda = 4 * C; m2m.table = T_M2M;
+    m2m.src = BUF_MP; m2m.dst = BUF_MP;
+    for (long long i = 0; i < NB; ++i) {
+      if (B[i].level != l || B[i].leaf >= 0) continue;
+      for (int ch = 0; ch < nch; ++ch) {
+        if (ch == 0 && !kact(l)) continue;
+        m2m.entries.push_back({(long long)(l * T->m2m_stride_lvl() + ch * T->m2m_stride_ch()),
+                               (long long)B[i].child0 * E + ch * C, i * E + ch * C});
+      }
+    }
+    if ((rc = upload_gemm(tr, m2m, s))) return rc;
+  }
+  tr->cur_stage = VP_STAGE_M2L;
+  if ((rc = upload_gemm(tr, m2l, s))) return rc;
+  if ((rc = upload_gemm(tr, s2l, s))) return rc;
+  tr->cur_stage = VP_STAGE_DOWNWARD;
+  {
+    HostReduce r;
+    r.M = C; r.dst = BUF_LOC; r.src = BUF_LSLOT;
+    r.ptr.push_back(0);
+    for (long long i = 0; i < NB; ++i) {
+      if (B[i].level < 2) continue;
+      for (int ch = 0; ch < nch; ++ch) {
+        r.dst_off.push_back(i * E + ch * C);
+        for (long long o : lsl[(size_t)i * nch + ch]) r.slot.push_back(o);
+        r.ptr.push_back((long long)r.slot.size());
+      }
+    }
+    if ((rc = upload_reduce(tr, r, s))) return rc;
+  }
+  for (int l = 3; l <= P.max_level; ++l) {
+    HostGemm l2l;
+    l2l.M = C; l2l.K = C; l2l.lda = C; l2l.accumulate = 1; l2l.table = T_L2L; l2l.src = BUF_LOC; l2l.dst = BUF_LOC;
+    for (long long i = 0; i < NB; ++i) {
+      if (B[i].level != l) continue;
+      const int par = B[i].parent;
+      const int q = (int)(i - B[par].child0);
+      for (int ch = 0; ch < nch; ++ch) {
+        if (ch == 0 && !kact(l - 1)) continue;
+        l2l.entries.push_back({(long long)((l - 1) * T->l2l_stride_lvl() + q * T->l2l_stride_q() + ch * T->l2l_stride_ch()),
+                               (long long)par * E + ch * C, i * E + ch * C});
+      }
+    }
+    if ((rc = upload_gemm(tr, l2l, s))) return rc;
+  }
+  tr->cur_stage = VP_STAGE_TARGETS;
+  if ((rc = upload_gemm(tr, l2t, s))) return rc;
+  if ((rc = upload_gemm(tr, m2t, s))) return rc;
+  tr->cur_stage = VP_STAGE_NEAR;
+  if (T->precision == VP_PREC_SPLIT) {
+    if ((rc = split_plan_build(tr, P, near_slot, s))) return rc;
+    tr->steps.push_back({3, 0, tr->cur_stage});
+    tr->flops[tr->cur_stage] += 2.0 * 3 * n * (double)n * (double)near_slot.size();
+  } else {
+    if ((rc = upload_gemm(tr, nearg, s))) return rc;
+  }
+  tr->cur_stage = VP_STAGE_OUTPUT;
+  {
+    HostReduce r;
+    r.M = 3 * n; r.final_out = 1; r.src = BUF_USLOT;
+    r.ptr.push_back(0);
+    for (int k = 0; k < tr->n_leaves; ++k) {
+      const int bi = P.leaf_box[k];
+      r.dst_off.push_back((long long)k * n);
+      for (long long o : usl[bi]) r.slot.push_back(o);
+      r.ptr.push_back((long long)r.slot.size());
+    }
+    if ((rc = upload_reduce(tr, r, s))) return rc;
+  }
+  return VP_OK;
+}
+
+int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  const vp_tables_s* T = tr->T;
+  int stage = -1;
+  const double* bufs_c[BUF_COUNT] = {f, tr->mp, tr->loc, tr->lslot, tr->uslot};
+  double* bufs[BUF_COUNT] = {nullptr, tr->mp, tr->loc, tr->lslot, tr->uslot};
+  for (const Step& st : tr->steps) {
+    if (ev) {
+      while (stage < st.stage) { ++stage; TRY(cudaEventRecord(ev[stage], s)); }
+    }
+    if (st.kind == 2) {
+      TRY(cudaMemsetAsync(tr->mp, 0, (size_t)tr->n_boxes * T->E * sizeof(double), s));
+    } else if (st.kind == 0) {
+      const DevGemm& d = tr->gemms[st.index];
+      GemmArgs a = d.args;
+      a.A = table_ptr(T, d.table);
+      a.X = bufs_c[d.src];
+      a.Y = bufs[d.dst];
+      k_gemm_gather_f64<<<d.n_tiles, 256, 0, s>>>(a);
+      TRY(cudaGetLastError());
+    } else if (st.kind == 1) {
+      const DevReduce& d = tr->reduces[st.index];
+      ReduceArgs a = d.args;
+      a.S = bufs_c[d.src];
+      if (a.final_out) { a.u = u; a.g = g; } else { a.Y = bufs[d.dst]; }
+      const int threads = a.M >= 256 ? 256 : ((a.M + 31) / 32) * 32;
+      k_reduce<<<d.n_dst, threads, 0, s>>>(a);
+      TRY(cudaGetLastError());
+    } else if (st.kind == 3) {
+      const int rc = split_near_run(tr, f, s);
+      if (rc) return rc;
+    }
+  }
+  if (ev) {
+    while (stage < VP_NSTAGES) { ++stage; TRY(cudaEventRecord(ev[stage], s)); }
+  }
+  return VP_OK;
+}
+
+}  // namespace vp
+
+using namespace vp;
+
+extern "C" int vp_tree_upload(vp_tables tables, double cx, double cy, int n_leaves, const int32_t* level,
+                              const int32_t* ix, const int32_t* iy, void* stream, vp_tree* out) {
+  if (!out) return VP_ERR_ARG;
+  *out = nullptr;
+  if (!tables || !level || !ix || !iy || n_leaves < 1 || !std::isfinite(cx) || !std::isfinite(cy)) return VP_ERR_ARG;
+  TreePlan P;
+  int rc = build_plan(n_leaves, level, ix, iy, tables->levels, P);
+  if (rc != VP_OK) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::unique_ptr<vp_tree_s> tr(new (std::nothrow) vp_tree_s());
+  if (!tr) return VP_ERR_OOM;
+  tr->T = tables;
+  tr->n_leaves = n_leaves;
+  tr->n_boxes = (int)P.boxes.size();
+  tr->max_level = P.max_level;
+  tr->N = (long long)n_leaves * tables->n;
+  tr->cx = cx; tr->cy = cy;
+  auto fail = [&](int code) { vp_tree_free(tr.release()); return code; };
+  {
+    std::vector<int> lv(level, level + n_leaves), xx(ix, ix + n_leaves), yy(iy, iy + n_leaves);
+    if ((rc = dev_upload(tr.get(), lv, &tr->d_lv, s))) return fail(rc);
+    if ((rc = dev_upload(tr.get(), xx, &tr->d_ix, s))) return fail(rc);
+    if ((rc = dev_upload(tr.get(), yy, &tr->d_iy, s))) return fail(rc);
+    std::vector<double> xi(tables->p), w(tables->p);
+    gauss_legendre_host(tables->p, xi.data(), w.data());
+    if ((rc = dev_upload(tr.get(), xi, &tr->d_xi, s))) return fail(rc);
+  }
+  if ((rc = build_tree(tr.get(), P, s))) return fail(rc);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { set_last_cuda(e); return fail(VP_ERR_CUDA); }
+  *out = tr.release();
+  return VP_OK;
+}
+
+extern "C" int vp_tree_size(vp_tree tree, int64_t* n_leaves, int64_t* n_nodes) {
+  if (!tree) return VP_ERR_ARG;
+  if (n_leaves) *n_leaves = tree->n_leaves;
+  if (n_nodes) *n_nodes = tree->N;
+  return VP_OK;
+}
+
+extern "C" int vp_tree_nodes(vp_tree tree, double* xy, void* stream) {
+  if (!tree || !xy) return VP_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const vp_tables_s* T = tree->T;
+  const long long N = tree->N;
+  k_nodes<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(T->p, tree->n_leaves, tree->cx - 0.5 * T->side,
+                                                     tree->cy - 0.5 * T->side, T->side, tree->d_lv, tree->d_ix,
+                                                     tree->d_iy, tree->d_xi, N, xy);
+  TRY(cudaGetLastError());
+  return VP_OK;
+}
+
+extern "C" int vp_eval(vp_tree tree, const double* f, double* u, double* gradu, void* stream) {
+  if (!tree || !f || !u || !gradu) return VP_ERR_ARG;
+  return run_steps(tree, f, u, gradu, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int vp_eval_timed(vp_tree tree, const double* f, double* u, double* gradu, void* stream,
+                             float* stage_ms) {
+  if (!tree || !f || !u || !gradu || !stage_ms) return VP_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t ev[VP_NSTAGES + 1];
+  int made = 0;
+  int rc = VP_OK;
+  for (; made <= VP_NSTAGES; ++made) {
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) { rc = VP_ERR_CUDA; break; }
+  }
+  if (rc == VP_OK) rc = run_steps(tree, f, u, gradu, s, ev);
+  if (rc == VP_OK) {
+    cudaError_t e = cudaEventSynchronize(ev[VP_NSTAGES]);
+    if (e != cudaSuccess) { set_last_cuda(e); rc = VP_ERR_CUDA; }
+  }
+  for (int k = 0; rc == VP_OK && k < VP_NSTAGES; ++k) {
+    if (cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]) != cudaSuccess) rc = VP_ERR_CUDA;
+  }
+  for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+  return rc;
+}
+
+extern "C" int vp_tree_stats(vp_tree tree, int64_t* launches, double* stage_flops) {
+  if (!tree) return VP_ERR_ARG;
+  if (launches) {
+    int64_t c = 0;
+    for (const Step& st : tree->steps) c += (st.kind == 3) ? split_launches(tree) : 1;
+    *launches = c;
+  }
+  if (stage_flops)
+    for (int k = 0; k < VP_NSTAGES; ++k) stage_flops[k] = tree->flops[k];
+  return VP_OK;
+}
+
+extern "C" int vp_eval_host(vp_tree tree, const double* f, double* u, double* gradu, void* stream) {
+  if (!tree || !f || !u || !gradu) return VP_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t N = (size_t)tree->N;
+  if (!tree->d_f) {
+    TRY(cudaMalloc(&tree->d_f, N * sizeof(double)));
+    tree->allocs.push_back(tree->d_f);
+    TRY(cudaMalloc(&tree->d_u, 3 * N * sizeof(double)));
+    tree->allocs.push_back(tree->d_u);
+    tree->d_g = tree->d_u + N;
+  }
+  TRY(cudaMemcpyAsync(tree->d_f, f, N * sizeof(double), cudaMemcpyHostToDevice, s));
+  const int rc = run_steps(tree, tree->d_f, tree->d_u, tree->d_g, s);
+  if (rc) return rc;
+  TRY(cudaMemcpyAsync(u, tree->d_u, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRY(cudaMemcpyAsync(gradu, tree->d_g, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  return VP_OK;
+}
+
+extern "C" void vp_tree_free(vp_tree tree) {
+  if (!tree) return;
+  if (tree->split_plan) split_plan_free(tree);
+  for (void* p : tree->allocs) cudaFree(p);
+  delete tree;
+}
+
+extern "C" const char* vp_strerror(int code) {
+  switch (code) {
+    case VP_OK: return "ok";
+    case VP_ERR_ARG: return "invalid argument";
+    case VP_ERR_TREE_UNBALANCED: return "adjacent leaves differ by more than one level";
+    case VP_ERR_LEVELS: return "a leaf is deeper than the tables";
+    case VP_ERR_OOM: return "out of memory";
+    case VP_ERR_CUDA: return "CUDA runtime error";
+    case VP_ERR_TREE: return "leaves overlap, leave gaps or lie outside the root box";
+    case VP_ERR_TIMEOUT: return "a bounded device wait ran out";
+  }
+  return "unknown error";
+}
