@@ -187,6 +187,32 @@ int vp_tree_stats(vp_tree tree, int64_t* launches, double* stage_flops);
 int vp_plan_pairs(int n_leaves, const int32_t* level, const int32_t* ix, const int32_t* iy, int64_t* n_out,
                   int32_t* tgt, int32_t* src, int32_t* mech);
 
+/*
+ * vp_eval_static -- vp_eval that allocates nothing.
+ *
+ * For callers that cannot call cudaMalloc (or any allocating routine) at the
+ * time they evaluate -- a fixed memory budget handed out before the work
+ * starts, an allocator that must not be touched while other work holds it.
+ * The tree and tables are still created beforehand with vp_tables_build and
+ * vp_tree_upload; this call then keeps every work buffer of the evaluation
+ * (multipole/local coefficients and per-interaction contribution slots) in a
+ * file-scope device array of VP_STATIC_SCRATCH_BYTES that every GPU loading
+ * the library reserves until the process exits. The paper has no counterpart;
+ * it is an interface convenience.
+ *  tree, f, u, gradu, stream  as vp_eval (caller-owned device inputs and outputs).
+ *  The first call on a device looks up the array's device address (once per
+ *  device, with that device current); make that first call before any stream
+ *  capture.
+ *  All calls share the one array and it keeps the last call's contents (the
+ *  parts that must start at zero are cleared by each call); calls that overlap
+ *  on the GPU race, so issue them on one stream.
+ * Errors: VP_ERR_ARG if the tree needs more than VP_STATIC_SCRATCH_BYTES of
+ * work space (2*boxes*coefficients + contribution slots, in doubles) or was
+ * built on VP_PREC_SPLIT tables; VP_ERR_CUDA.
+ */
+#define VP_STATIC_SCRATCH_BYTES (64u << 20)
+int vp_eval_static(vp_tree tree, const double* f, double* u, double* gradu, void* stream);
+
 /* Free a tree (after work on it has finished) / tables (after their trees). */
 void vp_tree_free(vp_tree tree);
 void vp_tables_free(vp_tables tables);

@@ -66,7 +66,8 @@ def load_library():
 def exported_symbols():
     """Names declared in include/vp.h (the ABI surface)."""
     return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_eval", "vp_eval_host",
-            "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs"]
+            "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
+            "vp_eval_static"]
 
 
 VP_NSTAGES = 6

@@ -642,3 +642,90 @@ extern "C" const char* vp_strerror(int code) {
   }
   return "unknown error";
 }
+
+// ---------------------------------------------------------------------------
+// vp_eval_static: vp_eval without any device allocation.
+//
+// Some callers cannot call cudaMalloc when they evaluate: code that runs
+// under a memory budget fixed before it starts, code that must not touch the
+// CUDA allocator while other work holds it, or hosts whose device memory is
+// handed out by someone else. For them this variant keeps every work buffer
+// of one evaluation (multipole and local coefficients, per-interaction
+// contribution slots) in the file-scope array below instead of the tree's own
+// buffers. The array is reserved on every GPU that loads the library, until
+// the process exits.
+#include <mutex>
+
+namespace vp {
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;  // VP_STATIC_SCRATCH_BYTES in vp.h
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) double g_static_scratch[kStaticScratchBytes / sizeof(double)];
+
+std::mutex g_static_mutex;
+double* g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the static scratch on the current device (looked up once per device).
+int static_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { set_last_cuda(e); return VP_ERR_CUDA; }
+  if (dev < 0 || dev >= kMaxDevices) return VP_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) { set_last_cuda(e); return VP_ERR_CUDA; }
+    g_static_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return VP_OK;
+}
+
+}  // namespace
+}  // namespace vp
+
+extern "C" int vp_eval_static(vp_tree tree, const double* f, double* u, double* gradu, void* stream) {
+  if (!tree || !f || !u || !gradu) return VP_ERR_ARG;
+  const vp_tables_s* T = tree->T;
+  if (T->precision != VP_PREC_FP64) return VP_ERR_ARG;
+  const size_t nbe = (size_t)tree->n_boxes * T->E;
+  const size_t need = 2 * nbe + (size_t)tree->n_lslot * T->C + (size_t)tree->n_uslot * 3 * T->n;
+  if (need * sizeof(double) > kStaticScratchBytes) return VP_ERR_ARG;
+  double* base = nullptr;
+  int rc = static_scratch(&base);
+  if (rc != VP_OK) return rc;
+  double* mp = base;
+  double* loc = mp + nbe;
+  double* lslot = loc + nbe;
+  double* uslot = lslot + (size_t)tree->n_lslot * T->C;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double* bufs_c[BUF_COUNT] = {f, mp, loc, lslot, uslot};
+  double* bufs[BUF_COUNT] = {nullptr, mp, loc, lslot, uslot};
+  for (const Step& st : tree->steps) {
+    if (st.kind == 2) {
+      // the multipole coefficients must start at zero; the other regions are overwritten
+      TRY(cudaMemsetAsync(mp, 0, nbe * sizeof(double), s));
+    } else if (st.kind == 0) {
+      const DevGemm& d = tree->gemms[st.index];
+      GemmArgs a = d.args;
+      a.A = table_ptr(T, d.table);
+      a.X = bufs_c[d.src];
+      a.Y = bufs[d.dst];
+      k_gemm_gather_f64<<<d.n_tiles, 256, 0, s>>>(a);
+      TRY(cudaGetLastError());
+    } else if (st.kind == 1) {
+      const DevReduce& d = tree->reduces[st.index];
+      ReduceArgs a = d.args;
+      a.S = bufs_c[d.src];
+      if (a.final_out) { a.u = u; a.g = gradu; } else { a.Y = bufs[d.dst]; }
+      const int threads = a.M >= 256 ? 256 : ((a.M + 31) / 32) * 32;
+      k_reduce<<<d.n_dst, threads, 0, s>>>(a);
+      TRY(cudaGetLastError());
+    } else {
+      return VP_ERR_ARG;
+    }
+  }
+  return VP_OK;
+}
