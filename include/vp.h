@@ -92,7 +92,11 @@ enum {
  *  order      expansion order P, 4 <= P <= 60 (40 gives about 12 digits, as in
  *             Sec. 3.2.1).
  *  precision  VP_PREC_FP64 (all contractions in FP64) or VP_PREC_SPLIT (the
- *             near-table contraction on tensor cores with sliced operands).
+ *             near-table, source-to-multipole, multipole-to-local,
+ *             source-to-local, local-to-target and multipole-to-target
+ *             contractions on the tensor cores from exact 8-bit slices of the
+ *             FP64 operands, accumulated in double-float; multipole-to-
+ *             multipole and local-to-local stay in FP64).
  *  stream     stream for the build kernels; the call synchronises it before
  *             returning.
  *  out        receives the handle; free with vp_tables_free.

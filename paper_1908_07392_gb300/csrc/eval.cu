@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "plan.h"
+#include "split.h"
 #include "vp_internal.h"
 
 namespace vp {
@@ -164,7 +165,10 @@ struct HostGemm {
   long long seg_stride = 0;
   int table = 0;  // which table array
   int src = 0, dst = 0;
-  struct Entry { long long a, s, d; };
+  // split precision: source vector family (-1: always FP64; 0: leaf values, 1: (box, channel)
+  // multipoles, 2: box locals) and output (0: double-float slot, 1: FP64 overwrite, 2: FP64 accumulate)
+  int split_vec = -1, out_mode = 0;
+  struct Entry { long long a, s, d, v = -1; };  // v: sliced-vector id (split), -1 = derived from s
   std::vector<Entry> entries;
 };
 
@@ -184,10 +188,26 @@ struct DevReduce {
   int dst, src, n_dst;
 };
 
+struct DevSplit {
+  SplitArgs args;
+  int table, vec, dst, n_tiles;
+};
+
+// Sliced-vector families (split precision): 0 leaf values (K = n), 1 (box, channel) multipoles (K = C),
+// 2 box locals (K = E), 3 stacked children multipoles of (parent, channel) (K = 4C), 4 (box, channel)
+// locals (K = C).
+constexpr int kVecFamilies = 5;
+struct DevSlice {
+  int family, buf, K, kseg;
+  long long seg_stride, cstride, n;
+  const long long* base;  // null: contiguous, b = v * cstride
+  const long long* vid;   // null: identity
+};
+
 enum Table { T_NEAR, T_S2M, T_L2T, T_M2M, T_L2L, T_M2L, T_M2T, T_S2L, T_SPLIT };
 
 struct Step {
-  int kind;   // 0 gemm, 1 reduce, 2 memset mp, 3 split-precision near (split.cu)
+  int kind;   // 0 gemm, 1 reduce, 2 memset mp, 3 slice vectors, 4 split gemm, 5 double-float reduce
   int index;
   int stage;  // VP_STAGE_* for timing
 };
@@ -210,8 +230,11 @@ struct vp_tree_s {
   std::vector<vp::Step> steps;
   int cur_stage = 0;        // stage tag given to steps as they are planned
   double flops[VP_NSTAGES] = {0};
-  // split-precision near pass (if the tables are VP_PREC_SPLIT)
-  void* split_plan = nullptr;
+  // split precision: sliced source vectors (leaf values, multipoles, locals) and their exponents
+  std::vector<vp::DevSplit> splits;
+  void* sv[vp::kVecFamilies] = {nullptr};
+  int* se[vp::kVecFamilies] = {nullptr};
+  std::vector<vp::DevSlice> slice_ops;
   // host staging for vp_eval_host
   double *h_f = nullptr, *h_u = nullptr;
   double *d_f = nullptr, *d_u = nullptr, *d_g = nullptr;
@@ -234,8 +257,11 @@ int dev_upload(vp_tree_s* tr, const std::vector<T>& v, T** out, cudaStream_t s) 
   return VP_OK;
 }
 
+int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s);
+
 int upload_gemm(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
   if (g.entries.empty()) return VP_OK;
+  if (tr->T->precision == VP_PREC_SPLIT && g.split_vec >= 0) return upload_split(tr, g, s);
   std::stable_sort(g.entries.begin(), g.entries.end(),
                    [](const HostGemm::Entry& x, const HostGemm::Entry& y) { return x.a < y.a; });
   std::vector<long long> a_off, src_off, dst_off;
@@ -270,6 +296,63 @@ int upload_gemm(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
   return VP_OK;
 }
 
+// Split-precision contraction: the same grouping, with tiles of the tensor-core kernel, matrix indices
+// instead of element offsets and vector indices instead of source offsets.
+int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
+  const vp_tables_s* T = tr->T;
+  std::stable_sort(g.entries.begin(), g.entries.end(),
+                   [](const HostGemm::Entry& x, const HostGemm::Entry& y) { return x.a < y.a; });
+  const long long mat_elems = (long long)g.M * g.lda;
+  const long long vec_len = g.split_vec == 0 ? T->n : (g.split_vec == 1 ? T->C : T->E);  // families 0-2
+  std::vector<long long> a_mat, src_vec, dst_off;
+  std::vector<SplitTile> tiles;
+  size_t i = 0;
+  while (i < g.entries.size()) {
+    size_t j = i;
+    while (j < g.entries.size() && g.entries[j].a == g.entries[i].a) ++j;
+    const int grp = (int)a_mat.size();
+    a_mat.push_back(g.entries[i].a / mat_elems);
+    const int col_begin = (int)src_vec.size();
+    for (size_t k = i; k < j; ++k) {
+      src_vec.push_back(g.entries[k].v >= 0 ? g.entries[k].v : g.entries[k].s / vec_len);
+      dst_off.push_back(g.entries[k].d);
+    }
+    const int ncols = (int)(j - i);
+    for (int m0 = 0; m0 < g.M; m0 += kSplitBM)
+      for (int c0 = 0; c0 < ncols; c0 += kSplitBN)
+        tiles.push_back({grp, m0, col_begin + c0, std::min(kSplitBN, ncols - c0)});
+    i = j;
+  }
+  DevSplit d{};
+  d.args.M = g.M; d.args.Kpad = split_kpad(g.K); d.args.out_mode = g.out_mode;
+  SplitTile* dt; long long *da, *ds, *dd;
+  int rc;
+  if ((rc = dev_upload(tr, tiles, &dt, s))) return rc;
+  if ((rc = dev_upload(tr, a_mat, &da, s))) return rc;
+  if ((rc = dev_upload(tr, src_vec, &ds, s))) return rc;
+  if ((rc = dev_upload(tr, dst_off, &dd, s))) return rc;
+  d.args.tiles = dt; d.args.a_mat = da; d.args.src_vec = ds; d.args.dst_off = dd;
+  d.table = g.table; d.vec = g.split_vec; d.dst = g.dst; d.n_tiles = (int)tiles.size();
+  tr->steps.push_back({4, (int)tr->splits.size(), tr->cur_stage});
+  tr->splits.push_back(d);
+  tr->flops[tr->cur_stage] += 2.0 * g.M * (double)g.K * (double)g.entries.size();
+  return VP_OK;
+}
+
+// A slicing step (split precision): contiguous over a whole family, or a listed subset.
+int add_slice(vp_tree_s* tr, int family, int buf, int K, int kseg, long long seg_stride, long long cstride,
+              long long n, const std::vector<long long>* base, const std::vector<long long>* vid, cudaStream_t s) {
+  DevSlice d{family, buf, K, kseg, seg_stride, cstride, n, nullptr, nullptr};
+  int rc;
+  long long* p = nullptr;
+  if (base) { if ((rc = dev_upload(tr, *base, &p, s))) return rc; d.base = p; }
+  if (vid) { if ((rc = dev_upload(tr, *vid, &p, s))) return rc; d.vid = p; }
+  if (n <= 0) return VP_OK;
+  tr->steps.push_back({3, (int)tr->slice_ops.size(), tr->cur_stage});
+  tr->slice_ops.push_back(d);
+  return VP_OK;
+}
+
 int upload_reduce(vp_tree_s* tr, HostReduce& r, cudaStream_t s) {
   if (r.dst_off.empty()) return VP_OK;
   DevReduce d{};
@@ -285,7 +368,8 @@ int upload_reduce(vp_tree_s* tr, HostReduce& r, cudaStream_t s) {
   }
   d.args.dst_off = a; d.args.ptr = b; d.args.slot = c;
   d.dst = r.dst; d.src = r.src; d.n_dst = (int)r.dst_off.size();
-  tr->steps.push_back({1, (int)tr->reduces.size(), tr->cur_stage});
+  // in split precision every slot producer writes double-float slots
+  tr->steps.push_back({tr->T->precision == VP_PREC_SPLIT ? 5 : 1, (int)tr->reduces.size(), tr->cur_stage});
   tr->flops[tr->cur_stage] += (double)r.M * (double)r.slot.size();
   tr->reduces.push_back(d);
   return VP_OK;
@@ -307,11 +391,6 @@ const double* table_ptr(const vp_tables_s* T, int t) {
 
 }  // namespace
 
-extern int split_plan_build(vp_tree_s* tr, const TreePlan& P, const std::vector<long long>& near_slot,
-                            cudaStream_t s);
-extern int split_near_run(vp_tree_s* tr, const double* f, cudaStream_t s);
-extern void split_plan_free(vp_tree_s* tr);
-extern int split_launches(const vp_tree_s* tr);
 
 int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   const vp_tables_s* T = tr->T;
@@ -325,7 +404,7 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   std::vector<std::vector<long long>> usl(B.size());
   long long nls = 0, nus = 0;
   HostGemm m2l, s2l, l2t, m2t, nearg, s2m;
-  m2l.M = C; m2l.K = C; m2l.lda = C; m2l.table = T_M2L; m2l.src = BUF_MP; m2l.dst = BUF_LSLOT;
+  m2l.M = C; m2l.K = C; m2l.lda = C; m2l.table = T_M2L; m2l.src = BUF_MP; m2l.dst = BUF_LSLOT; m2l.split_vec = 1;
   for (const Pair& v : P.V) {
     const int l = B[v.tgt].level;
     for (int ch = 0; ch < nch; ++ch) {
@@ -336,7 +415,7 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
                              (long long)v.src * E + ch * C, slot * C});
     }
   }
-  s2l.M = C; s2l.K = n; s2l.lda = n; s2l.table = T_S2L; s2l.src = BUF_F; s2l.dst = BUF_LSLOT;
+  s2l.M = C; s2l.K = n; s2l.lda = n; s2l.table = T_S2L; s2l.src = BUF_F; s2l.dst = BUF_LSLOT; s2l.split_vec = 0;
   for (const Pair& x : P.X) {
     const int l = B[x.tgt].level;
     for (int ch = 0; ch < nch; ++ch) {
@@ -348,16 +427,15 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
     }
   }
   nearg.M = 3 * n; nearg.K = n; nearg.lda = n; nearg.table = T_NEAR; nearg.src = BUF_F; nearg.dst = BUF_USLOT;
-  std::vector<long long> near_slot;
+  nearg.split_vec = 0;
   for (const Pair& u : P.U) {
     const int l = B[u.tgt].level;
     const long long slot = nus++;
     usl[u.tgt].push_back(slot * 3 * n);
-    near_slot.push_back(slot * 3 * n);
     nearg.entries.push_back({(long long)(l * T->near_stride_lvl() + u.pos * T->near_stride_pos()),
                              (long long)B[u.src].leaf * n, slot * 3 * n});
   }
-  m2t.M = 3 * n; m2t.K = C; m2t.lda = C; m2t.table = T_M2T; m2t.src = BUF_MP; m2t.dst = BUF_USLOT;
+  m2t.M = 3 * n; m2t.K = C; m2t.lda = C; m2t.table = T_M2T; m2t.src = BUF_MP; m2t.dst = BUF_USLOT; m2t.split_vec = 1;
   for (const Pair& w : P.W) {
     const int l = B[w.tgt].level;
     for (int ch = 0; ch < nch; ++ch) {
@@ -368,8 +446,9 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
                              (long long)w.src * E + ch * C, slot * 3 * n});
     }
   }
-  l2t.M = 3 * n; l2t.K = E; l2t.lda = E; l2t.table = T_L2T; l2t.src = BUF_LOC; l2t.dst = BUF_USLOT;
-  s2m.M = E; s2m.K = n; s2m.lda = n; s2m.table = T_S2M; s2m.src = BUF_F; s2m.dst = BUF_MP;
+  l2t.M = 3 * n; l2t.K = E; l2t.lda = E; l2t.table = T_L2T; l2t.src = BUF_LOC; l2t.dst = BUF_USLOT; l2t.split_vec = 2;
+  s2m.M = E; s2m.K = n; s2m.lda = n; s2m.table = T_S2M; s2m.src = BUF_F; s2m.dst = BUF_MP; s2m.split_vec = 0;
+  s2m.out_mode = 1;
   for (long long i = 0; i < NB; ++i) {
     const Box& b = B[i];
     if (b.leaf < 0 || b.level < 2) continue;
@@ -390,27 +469,46 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   tr->allocs.push_back(tr->lslot);
   TRY(cudaMalloc(&tr->uslot, std::max<long long>(1, nus * 3 * n) * sizeof(double)));
   tr->allocs.push_back(tr->uslot);
+  const bool split = T->precision == VP_PREC_SPLIT;
+  if (split) {
+    // sliced source vectors of every family
+    const long long nv[kVecFamilies] = {tr->n_leaves, NB * nch, NB, NB * nch, NB * nch};
+    const int kk[kVecFamilies] = {n, C, E, 4 * C, C};
+    for (int v = 0; v < kVecFamilies; ++v) {
+      TRY(cudaMalloc(&tr->sv[v], std::max<long long>(1, nv[v] * kSplitSlices * split_kpad(kk[v])) * 2));
+      tr->allocs.push_back(tr->sv[v]);
+      TRY(cudaMalloc(&tr->se[v], std::max<long long>(1, nv[v]) * sizeof(int)));
+      tr->allocs.push_back(tr->se[v]);
+    }
+  }
 
   int rc;
   // ---- steps, in pass order
   tr->cur_stage = VP_STAGE_UPWARD;
   tr->steps.push_back({2, 0, tr->cur_stage});  // clear multipoles
+  if (split && (rc = add_slice(tr, 0, BUF_F, n, n, 0, n, tr->n_leaves, nullptr, nullptr, s))) return rc;
   if ((rc = upload_gemm(tr, s2m, s))) return rc;
   for (int l = P.max_level - 1; l >= 2; --l) {
     HostGemm m2m;
     m2m.M = C; m2m.K = 4 * C; m2m.kseg = C; m2m.seg_stride = E; m2m.lda = 4 * C; m2m.table = T_M2M;
-    m2m.src = BUF_MP; m2m.dst = BUF_MP;
+    m2m.src = BUF_MP; m2m.dst = BUF_MP; m2m.split_vec = 3; m2m.out_mode = 1;
+    std::vector<long long> sbase, svid;
     for (long long i = 0; i < NB; ++i) {
       if (B[i].level != l || B[i].leaf >= 0) continue;
       for (int ch = 0; ch < nch; ++ch) {
         if (ch == 0 && !kact(l)) continue;
-        m2m.entries.push_back({(long long)(l * T->m2m_stride_lvl() + ch * T->m2m_stride_ch()),
-                               (long long)B[i].child0 * E + ch * C, i * E + ch * C});
+        const long long src = (long long)B[i].child0 * E + ch * C;
+        m2m.entries.push_back({(long long)(l * T->m2m_stride_lvl() + ch * T->m2m_stride_ch()), src,
+                               i * E + ch * C, i * nch + ch});
+        sbase.push_back(src);
+        svid.push_back(i * nch + ch);
       }
     }
+    if (split && (rc = add_slice(tr, 3, BUF_MP, 4 * C, C, E, 0, (long long)svid.size(), &sbase, &svid, s))) return rc;
     if ((rc = upload_gemm(tr, m2m, s))) return rc;
   }
   tr->cur_stage = VP_STAGE_M2L;
+  if (split && (rc = add_slice(tr, 1, BUF_MP, C, C, 0, C, NB * nch, nullptr, nullptr, s))) return rc;
   if ((rc = upload_gemm(tr, m2l, s))) return rc;
   if ((rc = upload_gemm(tr, s2l, s))) return rc;
   tr->cur_stage = VP_STAGE_DOWNWARD;
@@ -431,6 +529,8 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   for (int l = 3; l <= P.max_level; ++l) {
     HostGemm l2l;
     l2l.M = C; l2l.K = C; l2l.lda = C; l2l.accumulate = 1; l2l.table = T_L2L; l2l.src = BUF_LOC; l2l.dst = BUF_LOC;
+    l2l.split_vec = 4; l2l.out_mode = 2;
+    std::vector<long long> sbase, svid;
     for (long long i = 0; i < NB; ++i) {
       if (B[i].level != l) continue;
       const int par = B[i].parent;
@@ -438,22 +538,22 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
       for (int ch = 0; ch < nch; ++ch) {
         if (ch == 0 && !kact(l - 1)) continue;
         l2l.entries.push_back({(long long)((l - 1) * T->l2l_stride_lvl() + q * T->l2l_stride_q() + ch * T->l2l_stride_ch()),
-                               (long long)par * E + ch * C, i * E + ch * C});
+                               (long long)par * E + ch * C, i * E + ch * C, (long long)par * nch + ch});
+        if (q == 0) {  // each parent's local is sliced once
+          sbase.push_back((long long)par * E + ch * C);
+          svid.push_back((long long)par * nch + ch);
+        }
       }
     }
+    if (split && (rc = add_slice(tr, 4, BUF_LOC, C, C, 0, 0, (long long)svid.size(), &sbase, &svid, s))) return rc;
     if ((rc = upload_gemm(tr, l2l, s))) return rc;
   }
   tr->cur_stage = VP_STAGE_TARGETS;
+  if (split && (rc = add_slice(tr, 2, BUF_LOC, E, E, 0, E, NB, nullptr, nullptr, s))) return rc;
   if ((rc = upload_gemm(tr, l2t, s))) return rc;
   if ((rc = upload_gemm(tr, m2t, s))) return rc;
   tr->cur_stage = VP_STAGE_NEAR;
-  if (T->precision == VP_PREC_SPLIT) {
-    if ((rc = split_plan_build(tr, P, near_slot, s))) return rc;
-    tr->steps.push_back({3, 0, tr->cur_stage});
-    tr->flops[tr->cur_stage] += 2.0 * 3 * n * (double)n * (double)near_slot.size();
-  } else {
-    if ((rc = upload_gemm(tr, nearg, s))) return rc;
-  }
+  if ((rc = upload_gemm(tr, nearg, s))) return rc;
   tr->cur_stage = VP_STAGE_OUTPUT;
   {
     HostReduce r;
@@ -499,7 +599,32 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
       k_reduce<<<d.n_dst, threads, 0, s>>>(a);
       TRY(cudaGetLastError());
     } else if (st.kind == 3) {
-      const int rc = split_near_run(tr, f, s);
+      const DevSlice& d = tr->slice_ops[st.index];
+      const int rc = launch_slice_list(bufs_c[d.buf], d.base, d.vid, d.n, d.K, d.kseg, d.seg_stride, d.cstride,
+                                       tr->sv[d.family], tr->se[d.family], s);
+      if (rc) return rc;
+    } else if (st.kind == 4) {
+      const DevSplit& d = tr->splits[st.index];
+      const SplitTables* stt = static_cast<const SplitTables*>(T->near_split);
+      const SplitTable* tb = d.table == T_NEAR ? &stt->near : d.table == T_S2M ? &stt->s2m : d.table == T_L2T
+                             ? &stt->l2t : d.table == T_M2L ? &stt->m2l : d.table == T_M2T ? &stt->m2t
+                             : d.table == T_M2M ? &stt->m2m : d.table == T_L2L ? &stt->l2l : &stt->s2l;
+      SplitArgs a = d.args;
+      a.A = static_cast<const __half*>(tb->A);
+      a.ea = tb->ea;
+      a.B = static_cast<const __half*>(tr->sv[d.vec]);
+      a.eb = tr->se[d.vec];
+      a.Y = bufs[d.dst];
+      const int rc = launch_split_gemm(a, d.n_tiles, s);
+      if (rc) return rc;
+    } else if (st.kind == 5) {
+      const DevReduce& d = tr->reduces[st.index];
+      DFReduceArgs a{};
+      a.M = d.args.M; a.n = d.args.n; a.final_out = d.args.final_out; a.N = d.args.N;
+      a.dst_off = d.args.dst_off; a.ptr = d.args.ptr; a.slot = d.args.slot;
+      a.S = bufs_c[d.src];
+      if (a.final_out) { a.u = u; a.g = g; } else { a.Y = bufs[d.dst]; }
+      const int rc = launch_reduce_df(a, d.n_dst, s);
       if (rc) return rc;
     }
   }
@@ -597,7 +722,7 @@ extern "C" int vp_tree_stats(vp_tree tree, int64_t* launches, double* stage_flop
   if (!tree) return VP_ERR_ARG;
   if (launches) {
     int64_t c = 0;
-    for (const Step& st : tree->steps) c += (st.kind == 3) ? split_launches(tree) : 1;
+    for (const Step& st : tree->steps) { (void)st; ++c; }
     *launches = c;
   }
   if (stage_flops)
@@ -627,7 +752,6 @@ extern "C" int vp_eval_host(vp_tree tree, const double* f, double* u, double* gr
 
 extern "C" void vp_tree_free(vp_tree tree) {
   if (!tree) return;
-  if (tree->split_plan) split_plan_free(tree);
   for (void* p : tree->allocs) cudaFree(p);
   delete tree;
 }

@@ -1,0 +1,64 @@
+// Split-precision (sliced operand) contractions: shared declarations.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+struct vp_tables_s;
+
+namespace vp {
+
+constexpr int kSplitSlices = 6;  // 8-bit slices per operand: about 48 significant bits each
+
+struct SplitTile {
+  int group, m0, col0, ncol;
+};
+
+// One sliced operator family: slices [nmat][S][M][Kpad] (fp16) and row exponents [nmat][M].
+struct SplitTable {
+  void* A = nullptr;
+  int* ea = nullptr;
+  int M = 0, K = 0, Kpad = 0, nmat = 0;
+};
+
+struct SplitTables {
+  SplitTable near, s2m, l2t, m2l, m2t, s2l, m2m, l2l;
+};
+
+struct SplitArgs {
+  int M, Kpad, out_mode;       // out_mode 0: double-float slot (float2), 1: FP64 overwrite, 2: FP64 accumulate
+  const __half* A;
+  const int* ea;
+  const __half* B;              // sliced vectors [v][S][Kpad]
+  const int* eb;
+  void* Y;
+  const SplitTile* tiles;
+  const long long* a_mat;       // per group: matrix index
+  const long long* src_vec;     // per column: vector index
+  const long long* dst_off;     // per column: destination offset (elements of 8 bytes)
+};
+
+struct DFReduceArgs {
+  int M, n, final_out;
+  long long N;
+  const long long* dst_off;
+  const long long* ptr;
+  const long long* slot;
+  const void* S;
+  double* Y;
+  double* u;
+  double* g;
+};
+
+int build_split(vp_tables_s* T, cudaStream_t s);
+void free_split_tables(vp_tables_s* T);
+int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s);
+int launch_slice_list(const double* X, const long long* base, const long long* vid, long long nlist, int K, int kseg,
+                      long long seg_stride, long long cstride, void* out, int* eb, cudaStream_t s);
+int launch_reduce_df(const DFReduceArgs& a, int n_dst, cudaStream_t s);
+int split_kpad(int K);
+constexpr int kSplitBM = 128, kSplitBN = 48;
+
+}  // namespace vp

@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "special.cuh"
+#include "split.h"
 #include "vp_internal.h"
 
 namespace vp {
@@ -951,8 +952,9 @@ extern "C" int vp_tables_build(int kernel, double alpha, int p, int levels, doub
 
 extern "C" void vp_tables_free(vp_tables t) {
   if (!t) return;
+  vp::free_split_tables(t);
   for (void* ptr : {(void*)t->near, (void*)t->s2m, (void*)t->l2t, (void*)t->m2m, (void*)t->l2l, (void*)t->m2l,
-                    (void*)t->m2t, (void*)t->s2l, t->near_split, (void*)t->near_split_scale})
+                    (void*)t->m2t, (void*)t->s2l})
     if (ptr) cudaFree(ptr);
   delete t;
 }

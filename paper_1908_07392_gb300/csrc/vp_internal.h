@@ -51,11 +51,6 @@ void gauss_legendre_host(int n, double* x, double* w);
 
 }  // namespace vp
 
-struct vp_tables_s;
-namespace vp {
-// Slice the near tables for the split-precision contraction (split.cu).
-int build_split(vp_tables_s* T, cudaStream_t s);
-}  // namespace vp
 
 struct vp_tables_s {
   int kernel = 0;
@@ -76,9 +71,8 @@ struct vp_tables_s {
   double* m2l = nullptr;     // [L+1][40][nch][C][C]
   double* m2t = nullptr;     // [L+1][20][nch][3n][C]    (target level; source l+1)
   double* s2l = nullptr;     // [L+1][20][nch][C][n]     (target level; source leaf l-1)
-  // split-precision near tables (VP_PREC_SPLIT): slices of the near tables
+  // VP_PREC_SPLIT: sliced copies of the operator tables (vp::SplitTables, split.cu)
   void* near_split = nullptr;
-  double* near_split_scale = nullptr;
   int n_slices = 0;
 
   size_t near_stride_pos() const { return (size_t)3 * n * n; }
