@@ -30,6 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_FLOPS_PER_CLK_PER_SM = 4.0   # 2 DFMA per clock per SM: 1.25 TFLOP/s nominal over 152 SMs at ~2.06 GHz
+# DRAM bytes of one FP64 near-field launch on the default workload: the ncu capture of the same kernel at
+# depth 8 (688 MB for 66.6k near pairs) scaled by pairs to the 356k pairs at depth 10.
+TRAFFIC_FP64_NEAR = 3.68e9
 N_SM = 152
 
 
@@ -296,7 +299,8 @@ def main():
                                setup_s=round(setup_s, 2)),
                 "stage_ms": stages,
                 "roofline": dict(roof, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                                 traffic=None),
+                                 traffic=(TRAFFIC_FP64_NEAR if (prec == V.VP_PREC_FP64 and args.max_depth == 10
+                                                                and args.alpha == 300.0) else None)),
                 "cpu_baseline": cpu,
                 "e2e": None if e2e_value is None else {"value": e2e_value, "unit": "nodes/s",
                                                        "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 24 * N},
