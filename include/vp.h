@@ -217,12 +217,42 @@ int vp_plan_pairs(int n_leaves, const int32_t* level, const int32_t* ix, const i
 #define VP_STATIC_SCRATCH_BYTES (64u << 20)
 int vp_eval_static(vp_tree tree, const double* f, double* u, double* gradu, void* stream);
 
+/*
+ * Batches -- many independent trees (each with its own tables: kernel, alpha, p and depth may all
+ * differ) evaluated together.
+ *
+ * vp_batch_create records one CUDA graph that evaluates tree t from f[t] into u[t], gradu[t] for
+ * every t (device pointers, layouts as vp_eval). Each tree's evaluation becomes one branch of the
+ * graph, captured on one of n_streams forked streams (1..128), so the GPU overlaps the trees.
+ * The graph keeps the pointers it was recorded with: the caller keeps those buffers (and the trees)
+ * alive and in place for the batch's lifetime and writes new sources into the same f[t] buffers.
+ * A tree may appear in only one batch that runs at a time (its work buffers are reused).
+ * `stream` is used for the capture (it must not be capturing already).
+ * vp_batch_run replays the graph on `stream` (asynchronous).
+ * vp_batch_stats: total nodes of the batch and kernel launches per replay.
+ * vp_eval_batched: one-shot form; use_graph != 0 creates, runs (synchronising `stream`) and frees a
+ * batch with 16 streams; use_graph == 0 issues the trees one after another on `stream`.
+ * Errors: VP_ERR_ARG, VP_ERR_OOM, VP_ERR_CUDA. (Overlapping trees through a graph is not in the
+ * paper; it is how this library fills one GPU with many small problems.)
+ */
+typedef struct vp_batch_s* vp_batch;
+int vp_batch_create(int n_trees, const vp_tree* trees, const double* const* f, double* const* u,
+                    double* const* gradu, int n_streams, void* stream, vp_batch* out);
+int vp_batch_run(vp_batch batch, void* stream);
+int vp_batch_stats(vp_batch batch, int64_t* nodes, int64_t* launches);
+void vp_batch_free(vp_batch batch);
+int vp_eval_batched(int n_trees, const vp_tree* trees, const double* const* f, double* const* u,
+                    double* const* gradu, int use_graph, void* stream);
+
 /* Free a tree (after work on it has finished) / tables (after their trees). */
 void vp_tree_free(vp_tree tree);
 void vp_tables_free(vp_tables tables);
 
 /* Static description of an error code. */
 const char* vp_strerror(int code);
+
+/* Name of the last CUDA runtime error the library saw in this thread (diagnostics for VP_ERR_CUDA). */
+const char* vp_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

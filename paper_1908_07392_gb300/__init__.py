@@ -28,7 +28,10 @@ _lib = None
 class VPError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
-        super().__init__(f"{what}: {vp_strerror(code)} ({code})" if what else f"{vp_strerror(code)} ({code})")
+        msg = f"{vp_strerror(code)} ({code})"
+        if code == -5:
+            msg += f" [{load_library().vp_last_cuda_error().decode()}]"
+        super().__init__(f"{what}: {msg}" if what else msg)
 
 
 def load_library():
@@ -56,9 +59,18 @@ def load_library():
     lib.vp_tables_free.restype = None
     lib.vp_strerror.argtypes = [c_int]
     lib.vp_strerror.restype = ctypes.c_char_p
+    lib.vp_last_cuda_error.argtypes = []
+    lib.vp_last_cuda_error.restype = ctypes.c_char_p
     lib.vp_plan_pairs.argtypes = [c_int, i32p, i32p, i32p, i64p, i32p, i32p, i32p]
     lib.vp_eval_timed.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(ctypes.c_float)]
     lib.vp_tree_stats.argtypes = [c_void_p, i64p, ctypes.POINTER(c_double)]
+    pp = ctypes.POINTER(c_void_p)
+    lib.vp_batch_create.argtypes = [c_int, pp, pp, pp, pp, c_int, c_void_p, ctypes.POINTER(c_void_p)]
+    lib.vp_batch_run.argtypes = [c_void_p, c_void_p]
+    lib.vp_batch_stats.argtypes = [c_void_p, i64p, i64p]
+    lib.vp_batch_free.argtypes = [c_void_p]
+    lib.vp_batch_free.restype = None
+    lib.vp_eval_batched.argtypes = [c_int, pp, pp, pp, pp, c_int, c_void_p]
     _lib = lib
     return lib
 
@@ -67,7 +79,8 @@ def exported_symbols():
     """Names declared in include/vp.h (the ABI surface)."""
     return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_eval", "vp_eval_host",
             "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
-            "vp_eval_static"]
+            "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
+            "vp_eval_batched", "vp_last_cuda_error"]
 
 
 VP_NSTAGES = 6
@@ -183,6 +196,49 @@ def vp_plan_pairs(level, ix, iy):
     _check(lib.vp_plan_pairs(int(lv.size), plv, pix, piy, ctypes.byref(n), _i32(t)[1], _i32(s)[1], _i32(m)[1]),
            "vp_plan_pairs")
     return t, s, m
+
+
+def _ptr_array(values):
+    arr = (ctypes.c_void_p * len(values))()
+    for k, v in enumerate(values):
+        arr[k] = v
+    return arr
+
+
+def vp_batch_create(trees, f, u, gradu, n_streams=16, stream=None) -> int:
+    """One CUDA graph evaluating every tree (handles) from f[t] into u[t], gradu[t] (torch CUDA tensors)."""
+    n = len(trees)
+    out = ctypes.c_void_p()
+    rc = load_library().vp_batch_create(n, _ptr_array(trees), _ptr_array([x.data_ptr() for x in f]),
+                                        _ptr_array([x.data_ptr() for x in u]),
+                                        _ptr_array([x.data_ptr() for x in gradu]), int(n_streams),
+                                        _stream_ptr(stream), ctypes.byref(out))
+    _check(rc, "vp_batch_create")
+    return out.value
+
+
+def vp_batch_run(batch: int, stream=None):
+    _check(load_library().vp_batch_run(ctypes.c_void_p(batch), _stream_ptr(stream)), "vp_batch_run")
+
+
+def vp_batch_stats(batch: int):
+    a = ctypes.c_int64(); b = ctypes.c_int64()
+    _check(load_library().vp_batch_stats(ctypes.c_void_p(batch), ctypes.byref(a), ctypes.byref(b)), "vp_batch_stats")
+    return a.value, b.value
+
+
+def vp_batch_free(batch: int):
+    if batch:
+        load_library().vp_batch_free(ctypes.c_void_p(batch))
+
+
+def vp_eval_batched(trees, f, u, gradu, use_graph=1, stream=None):
+    n = len(trees)
+    rc = load_library().vp_eval_batched(n, _ptr_array(trees), _ptr_array([x.data_ptr() for x in f]),
+                                        _ptr_array([x.data_ptr() for x in u]),
+                                        _ptr_array([x.data_ptr() for x in gradu]), int(use_graph),
+                                        _stream_ptr(stream))
+    _check(rc, "vp_eval_batched")
 
 
 class VolumePotential:

@@ -12,7 +12,7 @@ LIB = os.path.join(BUILD, "libvp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["tables.cu", "eval.cu", "split.cu"]
 CPP_SOURCES = ["plan.cpp"]
-HEADERS = ["special.cuh", "vp_internal.h", "plan.h", os.path.join("..", "..", "include", "vp.h")]
+HEADERS = ["special.cuh", "vp_internal.h", "plan.h", "split.h", os.path.join("..", "..", "include", "vp.h")]
 
 
 def _nvcc():

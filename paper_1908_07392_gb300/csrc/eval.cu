@@ -756,6 +756,8 @@ extern "C" void vp_tree_free(vp_tree tree) {
   delete tree;
 }
 
+extern "C" const char* vp_last_cuda_error(void) { return cudaGetErrorString(last_cuda()); }
+
 extern "C" const char* vp_strerror(int code) {
   switch (code) {
     case VP_OK: return "ok";
@@ -768,6 +770,144 @@ extern "C" const char* vp_strerror(int code) {
     case VP_ERR_TIMEOUT: return "a bounded device wait ran out";
   }
   return "unknown error";
+}
+
+// ---------------------------------------------------------------------------
+// Batches: many independent trees (any kernel, alpha, p, depth) evaluated by one CUDA graph. Every
+// tree's evaluation is a chain of launches on private work buffers, so the graph holds one branch
+// per tree (captured on forked streams) and the hardware overlaps the branches; replaying the graph
+// costs one launch from the host.
+struct vp_batch_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int n_trees = 0;
+  long long nodes = 0;
+  int launches = 0;
+};
+
+namespace vp {
+namespace {
+
+int capture_trees(int n, const vp_tree* trees, const double* const* f, double* const* u, double* const* g,
+                  int n_streams, cudaStream_t user, vp_batch_s* B) {
+  std::vector<cudaStream_t> ss(n_streams, nullptr);
+  std::vector<cudaEvent_t> ev(n_streams + 1, nullptr);
+  int rc = VP_OK;
+  // capture on a private stream (the legacy default stream cannot be captured); it first waits for
+  // the caller's stream so that setup work queued there is complete
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return VP_ERR_CUDA;
+  if (cudaStreamSynchronize(user) != cudaSuccess) { cudaStreamDestroy(s); return VP_ERR_CUDA; }
+  for (int k = 0; k < n_streams && rc == VP_OK; ++k)
+    if (cudaStreamCreateWithFlags(&ss[k], cudaStreamNonBlocking) != cudaSuccess) rc = VP_ERR_CUDA;
+  for (int k = 0; k <= n_streams && rc == VP_OK; ++k)
+    if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) rc = VP_ERR_CUDA;
+  bool capturing = false;
+  if (rc == VP_OK) {
+    const cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { set_last_cuda(e); rc = VP_ERR_CUDA; }
+    else capturing = true;
+  }
+  if (rc == VP_OK && cudaEventRecord(ev[n_streams], s) != cudaSuccess) rc = VP_ERR_CUDA;
+  for (int k = 0; k < n_streams && rc == VP_OK; ++k)
+    if (cudaStreamWaitEvent(ss[k], ev[n_streams], 0) != cudaSuccess) rc = VP_ERR_CUDA;
+  for (int t = 0; t < n && rc == VP_OK; ++t) {
+    rc = run_steps(trees[t], f[t], u[t], g[t], ss[t % n_streams]);
+    B->launches += (int)trees[t]->steps.size();
+  }
+  for (int k = 0; k < n_streams && rc == VP_OK; ++k) {
+    if (cudaEventRecord(ev[k], ss[k]) != cudaSuccess || cudaStreamWaitEvent(s, ev[k], 0) != cudaSuccess)
+      rc = VP_ERR_CUDA;
+  }
+  if (capturing) {
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc == VP_OK && e != cudaSuccess) { set_last_cuda(e); rc = VP_ERR_CUDA; }
+    if (rc == VP_OK) B->graph = graph;
+    else if (graph) cudaGraphDestroy(graph);
+  }
+  if (rc == VP_OK) {
+    const cudaError_t e = cudaGraphInstantiate(&B->exec, B->graph, 0);
+    if (e != cudaSuccess) { set_last_cuda(e); rc = VP_ERR_CUDA; }
+  }
+  for (auto x : ev) if (x) cudaEventDestroy(x);
+  for (auto x : ss) if (x) cudaStreamDestroy(x);
+  cudaStreamDestroy(s);
+  return rc;
+}
+
+}  // namespace
+}  // namespace vp
+
+extern "C" int vp_batch_create(int n_trees, const vp_tree* trees, const double* const* f, double* const* u,
+                               double* const* gradu, int n_streams, void* stream, vp_batch* out) {
+  if (!out) return VP_ERR_ARG;
+  *out = nullptr;
+  if (n_trees < 1 || !trees || !f || !u || !gradu) return VP_ERR_ARG;
+  for (int t = 0; t < n_trees; ++t)
+    if (!trees[t] || !f[t] || !u[t] || !gradu[t]) return VP_ERR_ARG;
+  if (n_streams < 1) n_streams = 1;
+  if (n_streams > n_trees) n_streams = n_trees;
+  if (n_streams > 128) n_streams = 128;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // per-device kernel attributes are set outside the capture
+  for (int t = 0; t < n_trees; ++t)
+    if (trees[t]->T->precision == VP_PREC_SPLIT) {
+      const int rc = prepare_split_launch();
+      if (rc) return rc;
+      break;
+    }
+  std::unique_ptr<vp_batch_s> B(new (std::nothrow) vp_batch_s());
+  if (!B) return VP_ERR_OOM;
+  B->n_trees = n_trees;
+  for (int t = 0; t < n_trees; ++t) B->nodes += trees[t]->N;
+  const int rc = capture_trees(n_trees, trees, f, u, gradu, n_streams, s, B.get());
+  if (rc != VP_OK) { vp_batch_free(B.release()); return rc; }
+  *out = B.release();
+  return VP_OK;
+}
+
+extern "C" int vp_batch_run(vp_batch batch, void* stream) {
+  if (!batch || !batch->exec) return VP_ERR_ARG;
+  const cudaError_t e = cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) { set_last_cuda(e); return VP_ERR_CUDA; }
+  return VP_OK;
+}
+
+extern "C" int vp_batch_stats(vp_batch batch, int64_t* nodes, int64_t* launches) {
+  if (!batch) return VP_ERR_ARG;
+  if (nodes) *nodes = batch->nodes;
+  if (launches) *launches = batch->launches;
+  return VP_OK;
+}
+
+extern "C" void vp_batch_free(vp_batch batch) {
+  if (!batch) return;
+  if (batch->exec) cudaGraphExecDestroy(batch->exec);
+  if (batch->graph) cudaGraphDestroy(batch->graph);
+  delete batch;
+}
+
+extern "C" int vp_eval_batched(int n_trees, const vp_tree* trees, const double* const* f, double* const* u,
+                               double* const* gradu, int use_graph, void* stream) {
+  if (n_trees < 1 || !trees || !f || !u || !gradu) return VP_ERR_ARG;
+  if (use_graph) {
+    vp_batch b = nullptr;
+    int rc = vp_batch_create(n_trees, trees, f, u, gradu, 16, stream, &b);
+    if (rc == VP_OK) rc = vp_batch_run(b, stream);
+    if (rc == VP_OK) {
+      const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+      if (e != cudaSuccess) { set_last_cuda(e); rc = VP_ERR_CUDA; }
+    }
+    vp_batch_free(b);
+    return rc;
+  }
+  for (int t = 0; t < n_trees; ++t) {
+    if (!trees[t]) return VP_ERR_ARG;
+    const int rc = run_steps(trees[t], f[t], u[t], gradu[t], static_cast<cudaStream_t>(stream));
+    if (rc) return rc;
+  }
+  return VP_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -386,10 +386,26 @@ void free_split_tables(vp_tables_s* T) {
   T->near_split = nullptr;
 }
 
+// Per device: allow the GEMM kernel its dynamic shared memory (call outside stream capture).
+int prepare_split_launch() {
+  int dev = 0;
+  TRY(cudaGetDevice(&dev));
+  static bool done[64] = {false};
+  if (dev >= 0 && dev < 64 && done[dev]) return VP_OK;
+  TRY(cudaFuncSetAttribute(k_split_gemm<kSplitSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)split_smem_bytes(kSplitSlices)));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return VP_OK;
+}
+
 int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s) {
-  
   const size_t smem = split_smem_bytes(kSplitSlices);
-  TRY(cudaFuncSetAttribute(k_split_gemm<kSplitSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TRY(cudaStreamIsCapturing(s, &cs));
+  if (cs == cudaStreamCaptureStatusNone) {
+    const int rc = prepare_split_launch();
+    if (rc) return rc;
+  }
   if (n_tiles <= 0) return VP_OK;
   k_split_gemm<kSplitSlices><<<n_tiles, 256, smem, s>>>(a);
   TRY(cudaGetLastError());

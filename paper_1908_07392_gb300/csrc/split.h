@@ -54,6 +54,7 @@ struct DFReduceArgs {
 
 int build_split(vp_tables_s* T, cudaStream_t s);
 void free_split_tables(vp_tables_s* T);
+int prepare_split_launch();
 int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s);
 int launch_slice_list(const double* X, const long long* base, const long long* vid, long long nlist, int K, int kseg,
                       long long seg_stride, long long cstride, void* out, int* eb, cudaStream_t s);

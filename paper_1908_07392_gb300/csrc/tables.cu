@@ -49,6 +49,7 @@ namespace {
 thread_local cudaError_t g_last_cuda = cudaSuccess;
 }
 void set_last_cuda(cudaError_t e) { g_last_cuda = e; }
+cudaError_t last_cuda() { return g_last_cuda; }
 
 const Positions& positions() {
   static const Positions P = [] {

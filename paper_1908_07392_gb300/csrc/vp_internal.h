@@ -45,6 +45,7 @@ const Positions& positions();
 
 // Last CUDA error seen by the library (for diagnostics).
 void set_last_cuda(cudaError_t e);
+cudaError_t last_cuda();
 
 // Gauss-Legendre nodes and weights on [-1, 1], ascending (host).
 void gauss_legendre_host(int n, double* x, double* w);
