@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--workload", default="star", choices=["star", "batched"],
                     help="star: one adaptive tree (default); batched: 64 trees in one CUDA graph")
     ap.add_argument("--streams", type=int, default=16, help="graph branches for the batched workload")
+    ap.add_argument("--engine", default="auto", choices=["auto", "mma", "tcgen05"],
+                    help="split-precision GEMM engine: autotuned per launch, mma.sync, or tcgen05")
     return ap.parse_args()
 
 
@@ -187,6 +189,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def choose_engine(V, args, tree, f, u, g):
+    """Engine of the split-precision contractions; returns the number of launches on tcgen05."""
+    if args.precision != "split":
+        return 0
+    if args.engine == "mma":
+        V.vp_tree_set_engine(tree, V.ENGINE_MMA_SYNC)
+        return 0
+    if args.engine == "tcgen05":
+        V.vp_tree_set_engine(tree, V.ENGINE_TCGEN05)
+        return -1
+    return V.vp_autotune(tree, f, u, g)
+
+
 def run_batched(args):
     import torch
     import paper_1908_07392_gb300 as V
@@ -205,6 +220,7 @@ def run_batched(args):
     us = [torch.empty_like(f) for f in fs]
     gs = [torch.empty(2, f.numel(), dtype=torch.float64, device="cuda") for f in fs]
     trees = [vp.tree for vp in vps]
+    n_tc = sum(choose_engine(V, args, vp.tree, f, u, g) for vp, f, u, g in zip(vps, fs, us, gs))
     batch = V.vp_batch_create(trees, fs, us, gs, n_streams=args.streams)
     nodes, launches = V.vp_batch_stats(batch)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -251,6 +267,7 @@ def run_batched(args):
                                    "p in {8, 12, 16}, modified-Helmholtz kernel, Gaussian-sum sources",
                        "trees": len(ws), "nodes": int(nodes), "max_depth": int(max(w.tree.max_level for w in ws)),
                        "precision": args.precision, "streams": args.streams, "setup_s": round(setup_s, 1),
+                       "engine": args.engine if prec == V.VP_PREC_SPLIT else "fp64", "tcgen05_launches": n_tc,
                        "l2": "flushed before every timed step (512 MB write)"},
             "serial_ms_per_step": serial_ms / args.steps,
             "graph_speedup_vs_serial": serial_ms / graph_ms,
@@ -294,6 +311,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     launches, stage_flops = V.vp_tree_stats(vp.tree)
     stream = torch.cuda.current_stream()
+    n_tc = choose_engine(V, args, vp.tree, f, u, g)
 
     for _ in range(args.warmup):
         V.vp_eval(vp.tree, f, u, g)
@@ -358,7 +376,8 @@ def main():
         slices = 6  # kSplitSlices in the library
         achieved = near_flops * slices * (slices + 1) / 2 / (near_ms / 1000.0) / 1e12
         peak = measured_peaks().get("bf16_tflops", 1900.0)
-        roof = {"kernel": "k_split_gemm<6> (near-field tables, fp16 slices, fp32 accumulation)", "bound": "tensor",
+        roof = {"kernel": "split-precision near-field GEMM (6 fp16 slices, fp32 accumulation; engine per launch)",
+                "bound": "tensor",
                 "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json; fp16 has the same nominal rate)",
                 "fp64_equivalent_tflops": near_flops / (near_ms / 1000.0) / 1e12}
     stages = {name: round(statistics.mean(m[k] for m in stage_ms), 4) for k, name in enumerate(V.STAGE_NAMES)}
@@ -376,6 +395,8 @@ def main():
                 "vs_baseline": None, "dtype": "f64" if prec == V.VP_PREC_FP64 else "f64+f16-slices",
                 "data": "synthetic",
                 "config": dict(workload_desc(w), precision=args.precision, order=args.order,
+                               engine=args.engine if prec == V.VP_PREC_SPLIT else "fp64",
+                               tcgen05_launches=n_tc,
                                l2="flushed before every timed step (512 MB write)",
                                parallelism="replicas" if world > 1 else "single GPU",
                                setup_s=round(setup_s, 2)),

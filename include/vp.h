@@ -218,6 +218,25 @@ int vp_plan_pairs(int n_leaves, const int32_t* level, const int32_t* ix, const i
 int vp_eval_static(vp_tree tree, const double* f, double* u, double* gradu, void* stream);
 
 /*
+ * Engines of the split-precision contractions (trees on VP_PREC_SPLIT tables):
+ *  0  warp-level mma.sync m16n8k16 (fp16 in, fp32 accumulate in registers);
+ *  1  tcgen05.mma kind::f16 issued by one thread per CTA, six fp32 accumulators in tensor memory,
+ *     operands staged in shared memory; bounded mbarrier waits.
+ * Both compute the same exact slice sums. vp_tree_set_engine sets one engine for every launch of
+ * the tree (VP_ERR_ARG for other values). vp_autotune times each split-precision launch of one
+ * evaluation of `f` with both engines on `stream`, keeps the faster per launch, evaluates once more
+ * into u, gradu with the choice, and, if *n_tcgen05 is given, reports how many launches use engine 1.
+ * With cache_path (may be NULL) the choices are read from / appended to a text file keyed by
+ * (p, P, channels, operator, rows, padded K, tiles). Trees on FP64 tables are left unchanged.
+ * vp_device_status reads and clears the device flag a bounded wait sets when it gives up:
+ * VP_ERR_TIMEOUT if it was set, VP_OK otherwise (synchronising).
+ */
+int vp_tree_set_engine(vp_tree tree, int engine);
+int vp_autotune(vp_tree tree, const double* f, double* u, double* gradu, const char* cache_path, void* stream,
+                int* n_tcgen05);
+int vp_device_status(void);
+
+/*
  * Batches -- many independent trees (each with its own tables: kernel, alpha, p and depth may all
  * differ) evaluated together.
  *

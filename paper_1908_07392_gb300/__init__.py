@@ -59,6 +59,10 @@ def load_library():
     lib.vp_tables_free.restype = None
     lib.vp_strerror.argtypes = [c_int]
     lib.vp_strerror.restype = ctypes.c_char_p
+    lib.vp_tree_set_engine.argtypes = [c_void_p, c_int]
+    lib.vp_autotune.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_char_p, c_void_p,
+                                ctypes.POINTER(c_int)]
+    lib.vp_device_status.argtypes = []
     lib.vp_last_cuda_error.argtypes = []
     lib.vp_last_cuda_error.restype = ctypes.c_char_p
     lib.vp_plan_pairs.argtypes = [c_int, i32p, i32p, i32p, i64p, i32p, i32p, i32p]
@@ -80,7 +84,29 @@ def exported_symbols():
     return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_eval", "vp_eval_host",
             "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
-            "vp_eval_batched", "vp_last_cuda_error"]
+            "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status"]
+
+
+ENGINE_MMA_SYNC = 0
+ENGINE_TCGEN05 = 1
+
+
+def vp_tree_set_engine(tree: int, engine: int):
+    _check(load_library().vp_tree_set_engine(ctypes.c_void_p(tree), int(engine)), "vp_tree_set_engine")
+
+
+def vp_device_status():
+    _check(load_library().vp_device_status(), "vp_device_status")
+
+
+def vp_autotune(tree: int, f, u, gradu, cache_path=None, stream=None) -> int:
+    """Pick the faster split-precision engine per launch; returns how many launches use tcgen05."""
+    n = ctypes.c_int()
+    _check(load_library().vp_autotune(ctypes.c_void_p(tree), ctypes.c_void_p(f.data_ptr()),
+                                      ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(gradu.data_ptr()),
+                                      cache_path.encode() if cache_path else None, _stream_ptr(stream),
+                                      ctypes.byref(n)), "vp_autotune")
+    return n.value
 
 
 VP_NSTAGES = 6

@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -190,13 +191,16 @@ struct DevReduce {
 
 struct DevSplit {
   SplitArgs args;
-  int table, vec, dst, n_tiles;
+  int table, vec, dst;
+  const SplitTile* tiles[2];    // tile lists of the two engines
+  int n_tiles[2];
+  int engine = kEngineMmaSync;  // chosen per launch (vp_tree_set_engine, vp_autotune)
 };
 
 // Sliced-vector families (split precision): 0 leaf values (K = n), 1 (box, channel) multipoles (K = C),
-// 2 box locals (K = E), 3 stacked children multipoles of (parent, channel) (K = 4C), 4 (box, channel)
-// locals (K = C).
-constexpr int kVecFamilies = 5;
+// 2 box locals (K = E), 3 multipoles of children 0-1 of (parent, channel) (K = 2C), 4 (box, channel)
+// locals (K = C), 5 multipoles of children 2-3 of (parent, channel) (K = 2C).
+constexpr int kVecFamilies = 6;
 struct DevSlice {
   int family, buf, K, kseg;
   long long seg_stride, cstride, n;
@@ -204,7 +208,7 @@ struct DevSlice {
   const long long* vid;   // null: identity
 };
 
-enum Table { T_NEAR, T_S2M, T_L2T, T_M2M, T_L2L, T_M2L, T_M2T, T_S2L, T_SPLIT };
+enum Table { T_NEAR, T_S2M, T_L2T, T_M2M, T_L2L, T_M2L, T_M2T, T_S2L, T_M2M_LO, T_M2M_HI };
 
 struct Step {
   int kind;   // 0 gemm, 1 reduce, 2 memset mp, 3 slice vectors, 4 split gemm, 5 double-float reduce
@@ -305,7 +309,7 @@ int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
   const long long mat_elems = (long long)g.M * g.lda;
   const long long vec_len = g.split_vec == 0 ? T->n : (g.split_vec == 1 ? T->C : T->E);  // families 0-2
   std::vector<long long> a_mat, src_vec, dst_off;
-  std::vector<SplitTile> tiles;
+  std::vector<SplitTile> tiles[2];
   size_t i = 0;
   while (i < g.entries.size()) {
     size_t j = i;
@@ -318,21 +322,25 @@ int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
       dst_off.push_back(g.entries[k].d);
     }
     const int ncols = (int)(j - i);
-    for (int m0 = 0; m0 < g.M; m0 += kSplitBM)
-      for (int c0 = 0; c0 < ncols; c0 += kSplitBN)
-        tiles.push_back({grp, m0, col_begin + c0, std::min(kSplitBN, ncols - c0)});
+    for (int en = 0; en < 2; ++en)
+      for (int m0 = 0; m0 < g.M; m0 += kSplitBM)
+        for (int c0 = 0; c0 < ncols; c0 += kSplitBN[en])
+          tiles[en].push_back({grp, m0, col_begin + c0, std::min(kSplitBN[en], ncols - c0)});
     i = j;
   }
   DevSplit d{};
   d.args.M = g.M; d.args.Kpad = split_kpad(g.K); d.args.out_mode = g.out_mode;
-  SplitTile* dt; long long *da, *ds, *dd;
+  SplitTile *dt0, *dt1; long long *da, *ds, *dd;
   int rc;
-  if ((rc = dev_upload(tr, tiles, &dt, s))) return rc;
+  if ((rc = dev_upload(tr, tiles[0], &dt0, s))) return rc;
+  if ((rc = dev_upload(tr, tiles[1], &dt1, s))) return rc;
   if ((rc = dev_upload(tr, a_mat, &da, s))) return rc;
   if ((rc = dev_upload(tr, src_vec, &ds, s))) return rc;
   if ((rc = dev_upload(tr, dst_off, &dd, s))) return rc;
-  d.args.tiles = dt; d.args.a_mat = da; d.args.src_vec = ds; d.args.dst_off = dd;
-  d.table = g.table; d.vec = g.split_vec; d.dst = g.dst; d.n_tiles = (int)tiles.size();
+  d.args.a_mat = da; d.args.src_vec = ds; d.args.dst_off = dd;
+  d.tiles[0] = dt0; d.tiles[1] = dt1;
+  d.n_tiles[0] = (int)tiles[0].size(); d.n_tiles[1] = (int)tiles[1].size();
+  d.table = g.table; d.vec = g.split_vec; d.dst = g.dst;
   tr->steps.push_back({4, (int)tr->splits.size(), tr->cur_stage});
   tr->splits.push_back(d);
   tr->flops[tr->cur_stage] += 2.0 * g.M * (double)g.K * (double)g.entries.size();
@@ -472,8 +480,8 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   const bool split = T->precision == VP_PREC_SPLIT;
   if (split) {
     // sliced source vectors of every family
-    const long long nv[kVecFamilies] = {tr->n_leaves, NB * nch, NB, NB * nch, NB * nch};
-    const int kk[kVecFamilies] = {n, C, E, 4 * C, C};
+    const long long nv[kVecFamilies] = {tr->n_leaves, NB * nch, NB, NB * nch, NB * nch, NB * nch};
+    const int kk[kVecFamilies] = {n, C, E, 2 * C, C, 2 * C};
     for (int v = 0; v < kVecFamilies; ++v) {
       TRY(cudaMalloc(&tr->sv[v], std::max<long long>(1, nv[v] * kSplitSlices * split_kpad(kk[v])) * 2));
       tr->allocs.push_back(tr->sv[v]);
@@ -489,23 +497,43 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   if (split && (rc = add_slice(tr, 0, BUF_F, n, n, 0, n, tr->n_leaves, nullptr, nullptr, s))) return rc;
   if ((rc = upload_gemm(tr, s2m, s))) return rc;
   for (int l = P.max_level - 1; l >= 2; --l) {
-    HostGemm m2m;
-    m2m.M = C; m2m.K = 4 * C; m2m.kseg = C; m2m.seg_stride = E; m2m.lda = 4 * C; m2m.table = T_M2M;
-    m2m.src = BUF_MP; m2m.dst = BUF_MP; m2m.split_vec = 3; m2m.out_mode = 1;
-    std::vector<long long> sbase, svid;
-    for (long long i = 0; i < NB; ++i) {
-      if (B[i].level != l || B[i].leaf >= 0) continue;
-      for (int ch = 0; ch < nch; ++ch) {
-        if (ch == 0 && !kact(l)) continue;
-        const long long src = (long long)B[i].child0 * E + ch * C;
-        m2m.entries.push_back({(long long)(l * T->m2m_stride_lvl() + ch * T->m2m_stride_ch()), src,
-                               i * E + ch * C, i * nch + ch});
-        sbase.push_back(src);
-        svid.push_back(i * nch + ch);
+    if (!split) {
+      HostGemm m2m;
+      m2m.M = C; m2m.K = 4 * C; m2m.kseg = C; m2m.seg_stride = E; m2m.lda = 4 * C; m2m.table = T_M2M;
+      m2m.src = BUF_MP; m2m.dst = BUF_MP;
+      for (long long i = 0; i < NB; ++i) {
+        if (B[i].level != l || B[i].leaf >= 0) continue;
+        for (int ch = 0; ch < nch; ++ch) {
+          if (ch == 0 && !kact(l)) continue;
+          m2m.entries.push_back({(long long)(l * T->m2m_stride_lvl() + ch * T->m2m_stride_ch()),
+                                 (long long)B[i].child0 * E + ch * C, i * E + ch * C});
+        }
       }
+      if ((rc = upload_gemm(tr, m2m, s))) return rc;
+      continue;
     }
-    if (split && (rc = add_slice(tr, 3, BUF_MP, 4 * C, C, E, 0, (long long)svid.size(), &sbase, &svid, s))) return rc;
-    if ((rc = upload_gemm(tr, m2m, s))) return rc;
+    // split precision: children 0-1 (overwrite) then children 2-3 (accumulate), K = 2C each
+    for (int half = 0; half < 2; ++half) {
+      HostGemm m2m;
+      m2m.M = C; m2m.K = 2 * C; m2m.kseg = C; m2m.seg_stride = E; m2m.lda = 4 * C;
+      m2m.table = half ? T_M2M_HI : T_M2M_LO;
+      m2m.src = BUF_MP; m2m.dst = BUF_MP; m2m.split_vec = half ? 5 : 3; m2m.out_mode = half ? 2 : 1;
+      std::vector<long long> sbase, svid;
+      for (long long i = 0; i < NB; ++i) {
+        if (B[i].level != l || B[i].leaf >= 0) continue;
+        for (int ch = 0; ch < nch; ++ch) {
+          if (ch == 0 && !kact(l)) continue;
+          const long long src = (long long)(B[i].child0 + 2 * half) * E + ch * C;
+          m2m.entries.push_back({(long long)(l * T->m2m_stride_lvl() + ch * T->m2m_stride_ch()), src,
+                                 i * E + ch * C, i * nch + ch});
+          sbase.push_back(src);
+          svid.push_back(i * nch + ch);
+        }
+      }
+      if ((rc = add_slice(tr, half ? 5 : 3, BUF_MP, 2 * C, C, E, 0, (long long)svid.size(), &sbase, &svid, s)))
+        return rc;
+      if ((rc = upload_gemm(tr, m2m, s))) return rc;
+    }
   }
   tr->cur_stage = VP_STAGE_M2L;
   if (split && (rc = add_slice(tr, 1, BUF_MP, C, C, 0, C, NB * nch, nullptr, nullptr, s))) return rc;
@@ -570,6 +598,23 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   return VP_OK;
 }
 
+// Kernel arguments of one split-precision launch with the engine set in d.
+SplitArgs split_args(const vp_tree_s* tr, const DevSplit& d, double* const* bufs) {
+  const SplitTables* stt = static_cast<const SplitTables*>(tr->T->near_split);
+  const SplitTable* tb = d.table == T_NEAR ? &stt->near : d.table == T_S2M ? &stt->s2m : d.table == T_L2T
+                         ? &stt->l2t : d.table == T_M2L ? &stt->m2l : d.table == T_M2T ? &stt->m2t
+                         : d.table == T_M2M_LO ? &stt->m2m_lo : d.table == T_M2M_HI ? &stt->m2m_hi
+                         : d.table == T_L2L ? &stt->l2l : &stt->s2l;
+  SplitArgs a = d.args;
+  a.A = static_cast<const slice_t*>(tb->A);
+  a.ea = tb->ea;
+  a.B = static_cast<const slice_t*>(tr->sv[d.vec]);
+  a.eb = tr->se[d.vec];
+  a.Y = bufs[d.dst];
+  a.tiles = d.tiles[d.engine];
+  return a;
+}
+
 int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   const vp_tables_s* T = tr->T;
   int stage = -1;
@@ -606,16 +651,8 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
     } else if (st.kind == 4) {
       const DevSplit& d = tr->splits[st.index];
       const SplitTables* stt = static_cast<const SplitTables*>(T->near_split);
-      const SplitTable* tb = d.table == T_NEAR ? &stt->near : d.table == T_S2M ? &stt->s2m : d.table == T_L2T
-                             ? &stt->l2t : d.table == T_M2L ? &stt->m2l : d.table == T_M2T ? &stt->m2t
-                             : d.table == T_M2M ? &stt->m2m : d.table == T_L2L ? &stt->l2l : &stt->s2l;
-      SplitArgs a = d.args;
-      a.A = static_cast<const __half*>(tb->A);
-      a.ea = tb->ea;
-      a.B = static_cast<const __half*>(tr->sv[d.vec]);
-      a.eb = tr->se[d.vec];
-      a.Y = bufs[d.dst];
-      const int rc = launch_split_gemm(a, d.n_tiles, s);
+      SplitArgs a = split_args(tr, d, bufs);
+      const int rc = launch_split_gemm(a, d.n_tiles[d.engine], s, d.engine);
       if (rc) return rc;
     } else if (st.kind == 5) {
       const DevReduce& d = tr->reduces[st.index];
@@ -770,6 +807,136 @@ extern "C" const char* vp_strerror(int code) {
     case VP_ERR_TIMEOUT: return "a bounded device wait ran out";
   }
   return "unknown error";
+}
+
+// ---------------------------------------------------------------------------
+// Engine selection and autotuning of the split-precision contractions.
+
+extern "C" int vp_tree_set_engine(vp_tree tree, int engine) {
+  if (!tree || (engine != 0 && engine != 1)) return VP_ERR_ARG;
+  for (auto& d : tree->splits) d.engine = engine;
+  return VP_OK;
+}
+
+extern "C" int vp_device_status(void) {
+  int flag = 0;
+  const int rc = read_split_error(&flag);
+  if (rc) return rc;
+  return flag ? VP_ERR_TIMEOUT : VP_OK;
+}
+
+namespace vp {
+namespace {
+
+// Time every split-precision launch of one evaluation with the given engine (ms per launch).
+int time_split_launches(vp_tree_s* tr, const double* f, double* u, double* g, int engine, cudaStream_t s,
+                        std::vector<float>& ms) {
+  for (auto& d : tr->splits) d.engine = engine;
+  const int ns = (int)tr->splits.size();
+  std::vector<cudaEvent_t> ev(2 * ns, nullptr);
+  for (auto& x : ev) if (cudaEventCreate(&x) != cudaSuccess) return VP_ERR_CUDA;
+  int rc = run_steps(tr, f, u, g, s);  // warm up
+  const double* bufs_c[BUF_COUNT] = {f, tr->mp, tr->loc, tr->lslot, tr->uslot};
+  double* bufs[BUF_COUNT] = {nullptr, tr->mp, tr->loc, tr->lslot, tr->uslot};
+  (void)bufs_c;
+  for (int k = 0; rc == VP_OK && k < ns; ++k) {
+    DevSplit d = tr->splits[k];
+    d.engine = engine;
+    SplitArgs a = split_args(tr, d, bufs);
+    // accumulating outputs are only timed (their values are rebuilt by the next full evaluation)
+    if (cudaEventRecord(ev[2 * k], s) != cudaSuccess) rc = VP_ERR_CUDA;
+    if (rc == VP_OK) rc = launch_split_gemm(a, d.n_tiles[engine], s, engine);
+    if (rc == VP_OK && cudaEventRecord(ev[2 * k + 1], s) != cudaSuccess) rc = VP_ERR_CUDA;
+  }
+  if (rc == VP_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = VP_ERR_CUDA;
+  ms.assign(ns, 0.f);
+  for (int k = 0; rc == VP_OK && k < ns; ++k)
+    if (cudaEventElapsedTime(&ms[k], ev[2 * k], ev[2 * k + 1]) != cudaSuccess) rc = VP_ERR_CUDA;
+  for (auto x : ev) if (x) cudaEventDestroy(x);
+  return rc;
+}
+
+}  // namespace
+}  // namespace vp
+
+extern "C" int vp_autotune(vp_tree tree, const double* f, double* u, double* gradu, const char* cache_path,
+                           void* stream, int* n_tcgen05) {
+  if (!tree || !f || !u || !gradu) return VP_ERR_ARG;
+  if (tree->T->precision != VP_PREC_SPLIT || tree->splits.empty()) {
+    if (n_tcgen05) *n_tcgen05 = 0;
+    return VP_OK;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int ns = (int)tree->splits.size();
+  std::vector<int> choice(ns, -1);
+  // cache: one line per launch "key engine", key = p P nch table M Kpad tiles
+  auto key_of = [&](const DevSplit& d) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%d %d %d %d %d %d %d", tree->T->p, tree->T->P, tree->T->nch, d.table,
+                  d.args.M, d.args.Kpad, d.n_tiles[0]);
+    return std::string(buf);
+  };
+  std::vector<std::pair<std::string, int>> cache;
+  if (cache_path) {
+    if (FILE* fp = std::fopen(cache_path, "r")) {
+      char line[256];
+      while (std::fgets(line, sizeof(line), fp)) {
+        int a[7], eng;
+        if (std::sscanf(line, "%d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6], &eng) == 8) {
+          char k[160];
+          std::snprintf(k, sizeof(k), "%d %d %d %d %d %d %d", a[0], a[1], a[2], a[3], a[4], a[5], a[6]);
+          cache.emplace_back(k, eng);
+        }
+      }
+      std::fclose(fp);
+    }
+  }
+  bool need = false;
+  for (int k = 0; k < ns; ++k) {
+    const std::string key = key_of(tree->splits[k]);
+    for (auto& c : cache) if (c.first == key) choice[k] = c.second;
+    if (choice[k] < 0) need = true;
+  }
+  if (need) {
+    std::vector<float> t0, t1;
+    int rc = time_split_launches(tree, f, u, gradu, kEngineMmaSync, s, t0);
+    if (rc == VP_OK) rc = time_split_launches(tree, f, u, gradu, kEngineTcgen05, s, t1);
+    if (rc == VP_OK) rc = vp_device_status();
+    if (rc != VP_OK) {
+      vp_tree_set_engine(tree, kEngineMmaSync);
+      return rc;
+    }
+    // one decision per key: the engine with the smaller total time over the launches sharing it
+    for (int k = 0; k < ns; ++k) {
+      if (choice[k] >= 0) continue;
+      const std::string key = key_of(tree->splits[k]);
+      double a0 = 0.0, a1 = 0.0;
+      for (int m = 0; m < ns; ++m)
+        if (key_of(tree->splits[m]) == key) { a0 += t0[m]; a1 += t1[m]; }
+      const int c = (a1 < a0) ? kEngineTcgen05 : kEngineMmaSync;
+      for (int m = 0; m < ns; ++m)
+        if (choice[m] < 0 && key_of(tree->splits[m]) == key) choice[m] = c;
+    }
+    if (cache_path) {
+      if (FILE* fp = std::fopen(cache_path, "a")) {
+        for (int k = 0; k < ns; ++k) {
+          bool cached = false;
+          const std::string key = key_of(tree->splits[k]);
+          for (auto& c : cache) cached |= (c.first == key);
+          if (!cached) {
+            std::fprintf(fp, "%s %d\n", key.c_str(), choice[k]);
+            cache.emplace_back(key, choice[k]);
+          }
+        }
+        std::fclose(fp);
+      }
+    }
+  }
+  int ntc = 0;
+  for (int k = 0; k < ns; ++k) { tree->splits[k].engine = choice[k]; ntc += choice[k] == kEngineTcgen05; }
+  if (n_tcgen05) *n_tcgen05 = ntc;
+  // leave u, gradu holding a valid evaluation with the chosen engines
+  return run_steps(tree, f, u, gradu, s);
 }
 
 // ---------------------------------------------------------------------------

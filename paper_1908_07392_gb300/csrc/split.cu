@@ -5,25 +5,26 @@
 // error-free splitting of matrix products (Ozaki, Ogita, Oishi and Rump,
 // Numer. Algorithms 59, 2012):
 //   * each row r of A is scaled by 2^-ea[r] (ea[r] = exponent of the row's
-//     largest entry, so the scaled row lies in (-1, 1)) and cut into S slices
-//     of 8-bit integers: A[r,k] = 2^ea[r] * sum_i a_i[r,k] 2^(-8i) + rounding
-//     remainder below 2^(ea[r] - 8S - 1);
-//   * each vector x likewise with one exponent eb per vector;
-//   * the slices are stored exactly in fp16 (|a_1| <= 256, |a_i| <= 128 for
-//     i >= 2), so every product a_i b_j is exact and the tensor cores' fp32
-//     accumulation over K <= 256 terms stays below 2^24, i.e. exact, for the
-//     leading weights i + j <= 3 (and within 2^-24 of its own weight beyond);
-//   * products with the same i + j = d share the weight 2^(-8d), so they are
-//     accumulated together in fp32 and folded into a double-float (hi, lo)
-//     pair of fp32 numbers with error-free two-sums; the result is scaled by
-//     2^(ea[r] + eb) exactly. Terms with i + j > S + 1 are dropped.
-// The double-float results are stored in 8-byte slots and summed per target
-// in double-float by the reduction; FP64 arithmetic is needed only when a
-// result is written as an FP64 coefficient.
-#include <cuda_fp16.h>
+//     largest entry, so the scaled row lies in (-1, 1)) and written in S = 6
+//     balanced base-256 digits: A[r,k] = 2^ea[r] sum_i a_i[r,k] 2^(-8(i+1))
+//     up to 2^(ea[r] - 49); each vector x likewise with one exponent eb;
+//   * slice i holds a_i 2^(-8(i+1)) in bf16: every digit (|a_0| <= 256,
+//     |a_i| <= 128 for i >= 1) is exactly representable and the power-of-two
+//     scale keeps it exact, so every product of two slices is exact;
+//   * products with the same weight w = i + j are integer multiples of one
+//     power of two; their sum over K <= 256 stays below 2^24 of that unit for
+//     w <= 1 (and within 2^-24 of it at w = 2), so an fp32 accumulator per
+//     weight w = 0, 1, 2 holds it exactly; weights w >= 3 share a fourth
+//     accumulator whose rounding is below 2^-48 of the result;
+//   * the four sums are added in double-float (two fp32) and scaled by
+//     2^(ea[r] + eb) exactly. Products with i + j > S - 1 are dropped.
+// Two engines run the same arithmetic: warp-level mma.sync (m16n8k16 bf16),
+// and tcgen05.mma with the accumulators in tensor memory.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <new>
 #include <vector>
 
 #include "plan.h"
@@ -36,12 +37,14 @@ namespace {
 
 #define TRY(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { set_last_cuda(e_); return e_ == cudaErrorMemoryAllocation ? VP_ERR_OOM : VP_ERR_CUDA; } } while (0)
 
+constexpr int kAcc = 4;  // accumulators: weights 0, 1, 2 and the tail
+
 // Balanced base-256 digits of |x| * 2^(8S - e) (|x| < 2^e), taken straight from the FP64 bit pattern
 // with integer arithmetic: T = round(|x| 2^(8S-e)) < 2^(8S) (+1 from rounding), then the digits from the
 // least significant up, each moved into [-128, 127] with a carry, the leading one in [0, 256]; the sign
-// of x is applied to every digit. x = 2^e sum_i a_i 2^(-8i) up to 2^(e - 8S - 1). Digits are exact in fp16.
+// of x is applied to every digit. Slice i receives digit_i * 2^(-8(i+1)) (exact in bf16).
 template <int S>
-__device__ inline void digits(double x, int e, __half* out, size_t stride) {
+__device__ inline void digits(double x, int e, slice_t* out, size_t stride) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   int ex = (int)((bits >> 52) & 0x7ff);
   unsigned long long m = bits & ((1ull << 52) - 1);
@@ -63,7 +66,10 @@ __device__ inline void digits(double x, int e, __half* out, size_t stride) {
   dig[0] = (int)T;
   const bool neg = (bits >> 63) != 0;
 #pragma unroll
-  for (int i = 0; i < S; ++i) out[i * stride] = __int2half_rn(neg ? -dig[i] : dig[i]);
+  for (int i = 0; i < S; ++i) {
+    const float v = (float)(neg ? -dig[i] : dig[i]) * __int_as_float((127 - 8 * (i + 1)) << 23);
+    out[i * stride] = __float2bfloat16_rn(v);
+  }
 }
 
 // Exponent e with |v| < 2^e for v = max |x| > 0 (0 for v = 0).
@@ -74,10 +80,10 @@ __device__ inline int exponent_of(double v) {
 }
 
 // Slice rows of a batch of matrices: A[mat][r][k] (row stride lda, matrix stride mstride) ->
-// out[mat][s][r][Kpad] (fp16), ea[mat][r]. One warp per row.
+// out[mat][s][r][Kpad], ea[mat][r]. One warp per row.
 template <int S>
 __global__ void k_slice_rows(const double* __restrict__ A, long long mstride, int lda, int M, int K, int Kpad,
-                             int nmat, __half* __restrict__ out, int* __restrict__ ea) {
+                             int nmat, slice_t* __restrict__ out, int* __restrict__ ea) {
   const long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= (long long)nmat * M) return;
@@ -88,7 +94,7 @@ __global__ void k_slice_rows(const double* __restrict__ A, long long mstride, in
   for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(a[k]));
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = exponent_of(mx);
-  __half* o = out + (mat * S * M + r) * (long long)Kpad;
+  slice_t* o = out + (mat * S * M + r) * (long long)Kpad;
   const size_t sstride = (size_t)M * Kpad;
   for (int k = lane; k < Kpad; k += 32) digits<S>(k < K ? a[k] : 0.0, e, o + k, sstride);
   if (lane == 0) ea[mat * M + r] = e;
@@ -100,7 +106,7 @@ __global__ void k_slice_rows(const double* __restrict__ A, long long mstride, in
 template <int S>
 __global__ void k_slice_list(const double* __restrict__ X, const long long* __restrict__ base,
                              const long long* __restrict__ vid, long long nlist, int K, int kseg,
-                             long long seg_stride, long long cstride, int Kpad, __half* __restrict__ out,
+                             long long seg_stride, long long cstride, int Kpad, slice_t* __restrict__ out,
                              int* __restrict__ eb) {
   const long long v = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -114,18 +120,13 @@ __global__ void k_slice_list(const double* __restrict__ X, const long long* __re
   }
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = exponent_of(mx);
-  __half* o = out + id * (long long)S * Kpad;
+  slice_t* o = out + id * (long long)S * Kpad;
   for (int k = lane; k < Kpad; k += 32) {
     const int sg = k / kseg;
     digits<S>(k < K ? X[b + sg * seg_stride + (k - sg * kseg)] : 0.0, e, o + k, Kpad);
   }
   if (lane == 0) eb[id] = e;
 }
-
-// ------------------------------------------------------------------ tensor-core GEMM
-
-constexpr int kSBM = 128, kSBN = 48, kSKC = 32, kSPitch = kSKC + 8;  // halves per smem row
-constexpr int kWN = 24, kNT = kWN / 8;  // columns and n8 tiles per warp
 
 __device__ inline void df_add(float& hi, float& lo, float x) {
   const float s = __fadd_rn(hi, x);
@@ -137,6 +138,20 @@ __device__ inline void df_add(float& hi, float& lo, float x) {
   hi = t;
 }
 
+// Store one output element: double-float (h, l) times 2^e, as a double-float slot or into FP64.
+__device__ inline void store_out(const SplitArgs& a, long long dst, int row, float h, float l, int e) {
+  if (a.out_mode == 0) {
+    float2 o;
+    o.x = ldexpf(h, e);
+    o.y = ldexpf(l, e);
+    reinterpret_cast<float2*>(a.Y)[dst + row] = o;
+  } else {
+    const double val = ldexp((double)h + (double)l, e);
+    double* y = reinterpret_cast<double*>(a.Y) + dst + row;
+    *y = (a.out_mode == 2) ? *y + val : val;
+  }
+}
+
 __device__ inline void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   const int n = valid ? 16 : 0;
@@ -146,6 +161,11 @@ __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\
 template <int N>
 __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// ------------------------------------------------------------------ engine 0: mma.sync
+
+constexpr int kMBN = kSplitBN[kEngineMmaSync];          // 64
+constexpr int kMKC = 32, kMPitch = kMKC + 8;             // K chunk and shared row pitch (elements)
+
 __device__ inline void ldmatrix_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -153,14 +173,9 @@ __device__ inline void ldmatrix_x4(unsigned& r0, unsigned& r1, unsigned& r2, uns
                : "r"(a));
 }
 
-__device__ inline void ldmatrix_x2(unsigned& r0, unsigned& r1, const void* p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
-}
-
 __device__ inline void mma16816(float* c, const unsigned* a, const unsigned* b) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
@@ -169,123 +184,98 @@ __device__ inline void mma16816(float* c, const unsigned* a, const unsigned* b) 
 template <int S>
 __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __half* As = reinterpret_cast<__half*>(smem_raw);                       // [2][S][BM][pitch]
-  __half* Bs = As + 2 * S * kSBM * kSPitch;                                 // [2][S][BN][pitch]
+  slice_t* As = reinterpret_cast<slice_t*>(smem_raw);                  // [2][S][BM][pitch]
+  slice_t* Bs = As + 2 * S * kSplitBM * kMPitch;                        // [2][S][BN][pitch]
   const SplitTile tile = a.tiles[blockIdx.x];
   const long long mat = a.a_mat[tile.group];
-  const __half* Ag = a.A + mat * (long long)S * a.M * a.Kpad;
+  const slice_t* Ag = a.A + mat * (long long)S * a.M * a.Kpad;
   const int* ea = a.ea + mat * a.M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 3, wn = warp >> 2;  // 4 warps along M (32 rows), 2 along N (24 columns)
+  const int wm = warp & 3, wn = warp >> 2;  // 4 warps along M (32 rows), 2 along N (32 columns)
   const int gid = lane >> 2, tig = lane & 3;
 
   auto load_chunk = [&](int buf, int k0) {
-    // A: S slices x BM rows x KC halves = S*BM*4 16-byte pieces
-    for (int e = tid; e < S * kSBM * 4; e += 256) {
-      const int s = e / (kSBM * 4), rem = e % (kSBM * 4);
+    for (int e = tid; e < S * kSplitBM * 4; e += 256) {
+      const int sl = e / (kSplitBM * 4), rem = e % (kSplitBM * 4);
       const int r = rem >> 2, c = (rem & 3) * 8;
       const int gr = tile.m0 + r;
       const bool ok = gr < a.M;
-      const __half* src = Ag + ((long long)s * a.M + (ok ? gr : 0)) * a.Kpad + k0 + c;
-      cp_async16(As + ((buf * S + s) * kSBM + r) * kSPitch + c, src, ok);
+      const slice_t* src = Ag + ((long long)sl * a.M + (ok ? gr : 0)) * a.Kpad + k0 + c;
+      cp_async16(As + ((buf * S + sl) * kSplitBM + r) * kMPitch + c, src, ok);
     }
-    for (int e = tid; e < S * kSBN * 4; e += 256) {
-      const int s = e / (kSBN * 4), rem = e % (kSBN * 4);
+    for (int e = tid; e < S * kMBN * 4; e += 256) {
+      const int sl = e / (kMBN * 4), rem = e % (kMBN * 4);
       const int col = rem >> 2, c = (rem & 3) * 8;
       const bool ok = col < tile.ncol;
       const long long v = ok ? a.src_vec[tile.col0 + col] : 0;
-      const __half* src = a.B + (v * S + s) * (long long)a.Kpad + k0 + c;
-      cp_async16(Bs + ((buf * S + s) * kSBN + col) * kSPitch + c, src, ok);
+      const slice_t* src = a.B + (v * S + sl) * (long long)a.Kpad + k0 + c;
+      cp_async16(Bs + ((buf * S + sl) * kMBN + col) * kMPitch + c, src, ok);
     }
     cp_async_commit();
   };
 
-  // one fp32 accumulator per weight 2^(-8d), d = i + j = 2..S+1, kept over the whole K: the sums of
-  // integer products stay exact (below 2^24) for d <= 3 and are folded into double-float only at the end
-  float acc[S][2][kNT][4];
+  float acc[kAcc][2][4][4];
 #pragma unroll
-  for (int d = 0; d < S; ++d)
+  for (int w = 0; w < kAcc; ++w)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
-      for (int j = 0; j < kNT; ++j)
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[d][i][j][c] = 0.f;
+        for (int c = 0; c < 4; ++c) acc[w][i][j][c] = 0.f;
 
-  const int nchunks = a.Kpad / kSKC;
+  const int nchunks = a.Kpad / kMKC;
   load_chunk(0, 0);
   for (int ch = 0; ch < nchunks; ++ch) {
     const int buf = ch & 1;
     if (ch + 1 < nchunks) {
-      load_chunk(buf ^ 1, (ch + 1) * kSKC);
+      load_chunk(buf ^ 1, (ch + 1) * kMKC);
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
 #pragma unroll
-    for (int ks = 0; ks < kSKC / 16; ++ks) {
-      // B fragments in two halves of the slices (register budget), each A slice loaded once per half
-      constexpr int H = (S + 1) / 2;
+    for (int ks = 0; ks < kMKC / 16; ++ks) {
+      unsigned bf[S][4][2];
 #pragma unroll
-      for (int jh = 0; jh < 2; ++jh) {
-        unsigned bf[H][kNT][2];
+      for (int j = 0; j < S; ++j) {
+        const slice_t* Bb = Bs + ((buf * S + j) * kMBN + wn * 32) * kMPitch;
 #pragma unroll
-        for (int jj = 0; jj < H; ++jj) {
-          const int j = jh * H + jj;
-          if (j >= S) break;
-          const __half* Bb = Bs + ((buf * S + j) * kSBN + wn * kWN) * kSPitch;
+        for (int nt2 = 0; nt2 < 2; ++nt2) {
           unsigned r0, r1, r2, r3;
           ldmatrix_x4(r0, r1, r2, r3,
-                      Bb + ((lane & 7) + ((lane >> 4) << 3)) * kSPitch + ks * 16 + ((lane >> 3) & 1) * 8);
-          bf[jj][0][0] = r0; bf[jj][0][1] = r1;
-          bf[jj][1][0] = r2; bf[jj][1][1] = r3;
-          ldmatrix_x2(bf[jj][2][0], bf[jj][2][1], Bb + (16 + (lane & 7)) * kSPitch + ks * 16 + ((lane >> 3) & 1) * 8);
+                      Bb + (nt2 * 16 + (lane & 7) + ((lane >> 4) << 3)) * kMPitch + ks * 16 + ((lane >> 3) & 1) * 8);
+          bf[j][nt2 * 2][0] = r0; bf[j][nt2 * 2][1] = r1;
+          bf[j][nt2 * 2 + 1][0] = r2; bf[j][nt2 * 2 + 1][1] = r3;
         }
+      }
 #pragma unroll
-        for (int i = 0; i < S; ++i) {
-          if (i + jh * H >= S) break;
-          const __half* Ab = As + ((buf * S + i) * kSBM + wm * 32) * kSPitch;
-          unsigned af[2][4];  // two m16 tiles
+      for (int i = 0; i < S; ++i) {
+        const slice_t* Ab = As + ((buf * S + i) * kSplitBM + wm * 32) * kMPitch;
+        unsigned af[2][4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+          ldmatrix_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3],
+                      Ab + (mt * 16 + (lane & 15)) * kMPitch + ks * 16 + (lane >> 4) * 8);
+#pragma unroll
+        for (int j = 0; i + j < S; ++j) {
+          const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
 #pragma unroll
           for (int mt = 0; mt < 2; ++mt)
-            ldmatrix_x4(af[mt][0], af[mt][1], af[mt][2], af[mt][3],
-                        Ab + (mt * 16 + (lane & 15)) * kSPitch + ks * 16 + (lane >> 4) * 8);
 #pragma unroll
-          for (int jj = 0; jj < H; ++jj) {
-            const int j = jh * H + jj;  // slice indices i+1, j+1: weight index d - 2 = i + j
-            if (j >= S || i + j >= S) break;
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-              for (int nt = 0; nt < kNT; ++nt) mma16816(acc[i + j][mt][nt], af[mt], bf[jj][nt]);
-          }
+            for (int nt = 0; nt < 4; ++nt) mma16816(acc[w][mt][nt], af[mt], bf[j][nt]);
         }
       }
     }
     __syncthreads();
   }
 
-  float hi[2][kNT][4], lo[2][kNT][4];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-    for (int nt = 0; nt < kNT; ++nt)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        float h = 0.f, l = 0.f;
-#pragma unroll
-        for (int d = 0; d < S; ++d) df_add(h, l, __fmul_rn(acc[d][mt][nt][c], __int_as_float((127 - 8 * (d + 2)) << 23)));
-        hi[mt][nt][c] = h;
-        lo[mt][nt][c] = l;
-      }
-
-  // epilogue: scale by 2^(ea[row] + eb[col]) and store
-#pragma unroll
-  for (int nt = 0; nt < kNT; ++nt)
+  for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
     for (int cc = 0; cc < 2; ++cc) {
-      const int col = wn * kWN + nt * 8 + tig * 2 + cc;
+      const int col = wn * 32 + nt * 8 + tig * 2 + cc;
       if (col >= tile.ncol) continue;
       const long long v = a.src_vec[tile.col0 + col];
       const int eb = a.eb[v];
@@ -296,21 +286,218 @@ __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
         for (int rr = 0; rr < 2; ++rr) {
           const int row = tile.m0 + wm * 32 + mt * 16 + gid + rr * 8;
           if (row >= a.M) continue;
-          const int e = ea[row] + eb;
-          const float h = hi[mt][nt][rr * 2 + cc], l = lo[mt][nt][rr * 2 + cc];
-          if (a.out_mode == 0) {
-            float2 o;
-            o.x = ldexpf(h, e);
-            o.y = ldexpf(l, e);
-            reinterpret_cast<float2*>(a.Y)[dst + row] = o;
-          } else {
-            const double val = ldexp((double)h + (double)l, e);
-            double* y = reinterpret_cast<double*>(a.Y) + dst + row;
-            *y = (a.out_mode == 2) ? *y + val : val;
-          }
+          float h = 0.f, l = 0.f;
+#pragma unroll
+          for (int w = 0; w < kAcc; ++w) df_add(h, l, acc[w][mt][nt][rr * 2 + cc]);
+          store_out(a, dst, row, h, l, ea[row] + eb);
         }
     }
 }
+
+size_t mma_smem_bytes(int S) { return (size_t)2 * S * (kSplitBM + kMBN) * kMPitch * sizeof(slice_t); }
+
+// ------------------------------------------------------------------ engine 1: tcgen05
+//
+// One thread issues tcgen05.mma (kind::f16 with bf16 operands, M = 128, N = 128, K = 16) from
+// shared-memory descriptors into four fp32 accumulators in tensor memory (one per weight group);
+// operand tiles for one K step of 16 are staged by cp.async into a 4-stage ring in the canonical
+// K-major layout without swizzle (8 x 16-byte core matrices; the next core matrix along K is 128
+// bytes further, the next 8-row group 256 bytes further); tcgen05.commit arrives on the stage's
+// mbarrier when its MMAs are done, which frees the stage for the load three steps ahead. Every
+// mbarrier wait is bounded: on timeout the kernel raises a flag, waits (bounded) for its MMAs and
+// releases its tensor memory before returning.
+
+__device__ int g_split_error = 0;
+
+constexpr int kTcThreads = 128;
+constexpr int kTcN = kSplitBN[kEngineTcgen05];   // 128
+constexpr int kTcKC = 16;                         // K per stage
+constexpr int kTcStages = 4;
+constexpr int kTcCols = kAcc * kTcN;              // 512 tensor-memory columns
+constexpr int kTcA = kSplitBM * kTcKC;            // elements per A slice tile
+constexpr int kTcB = kTcN * kTcKC;                // elements per B slice tile
+static_assert(kTcCols <= 512, "tensor memory holds 512 columns");
+
+__device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline unsigned long long umma_desc(unsigned saddr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((saddr >> 4) & 0x3FFFu) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // version 1, no swizzle
+}
+
+__device__ inline void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier; false if it gave up (~2 s).
+__device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity));
+    if (done) return true;
+    if (clock64() - t0 > 4000000000ll) return false;
+  }
+}
+
+template <int S>
+__global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  slice_t* As = reinterpret_cast<slice_t*>(smem_raw);  // [stages][S][kTcA]
+  slice_t* Bs = As + kTcStages * S * kTcA;              // [stages][S][kTcB]
+  __shared__ __align__(8) unsigned long long mbar[kTcStages];
+  __shared__ unsigned tmem_base_sh;
+  __shared__ int abort_sh;
+  const SplitTile tile = a.tiles[blockIdx.x];
+  const long long mat = a.a_mat[tile.group];
+  const slice_t* Ag = a.A + mat * (long long)S * a.M * a.Kpad;
+  const int* ea = a.ea + mat * a.M;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_sh)),
+                 "n"(kTcCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kTcStages; ++s) mbar_init(&mbar[s], 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  const unsigned tmem = tmem_base_sh;
+  const int nk = a.Kpad / kTcKC;
+
+  // one cp.async group per K step (empty beyond the end, so that group counting stays uniform)
+  auto load_step = [&](int k) {
+    if (k < nk) {
+      const int st = k % kTcStages, k0 = k * kTcKC;
+      for (int e = tid; e < S * kSplitBM * 2; e += kTcThreads) {
+        const int sl = e / (kSplitBM * 2), rem = e % (kSplitBM * 2);
+        const int r = rem >> 1, c = rem & 1;
+        const int gr = tile.m0 + r;
+        const bool ok = gr < a.M;
+        const slice_t* src = Ag + ((long long)sl * a.M + (ok ? gr : 0)) * a.Kpad + k0 + c * 8;
+        slice_t* dst = As + (st * S + sl) * kTcA + ((r >> 3) * 2 + c) * 64 + (r & 7) * 8;
+        cp_async16(dst, src, ok);
+      }
+      for (int e = tid; e < S * kTcN * 2; e += kTcThreads) {
+        const int sl = e / (kTcN * 2), rem = e % (kTcN * 2);
+        const int col = rem >> 1, c = rem & 1;
+        const bool ok = col < tile.ncol;
+        const long long v = ok ? a.src_vec[tile.col0 + col] : 0;
+        const slice_t* src = a.B + (v * S + sl) * (long long)a.Kpad + k0 + c * 8;
+        slice_t* dst = Bs + (st * S + sl) * kTcB + ((col >> 3) * 2 + c) * 64 + (col & 7) * 8;
+        cp_async16(dst, src, ok);
+      }
+    }
+    cp_async_commit();
+  };
+
+  // instruction descriptor: D f32, A and B bf16, both K-major, N = 128, M = 128
+  const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcN >> 3) << 17) |
+                         ((unsigned)(kSplitBM >> 4) << 24);
+  bool ok = true;
+  for (int k = 0; k < kTcStages - 1; ++k) load_step(k);
+  for (int k = 0; k < nk && ok; ++k) {
+    const int st = k % kTcStages;
+    cp_async_wait<kTcStages - 2>();  // the group of step k has landed
+    asm volatile("fence.proxy.async.shared::cta;\n");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      const unsigned abase = smem_u32(As + st * S * kTcA), bbase = smem_u32(Bs + st * S * kTcB);
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const unsigned long long da = umma_desc(abase + i * kTcA * 2, 128, 256);
+#pragma unroll
+        for (int j = 0; i + j < S; ++j) {
+          const unsigned long long db = umma_desc(bbase + j * kTcB * 2, 128, 256);
+          const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
+          const unsigned d_tmem = tmem + (unsigned)(w * kTcN);
+          // the first product of each accumulator (step 0, i = 0, j = w) overwrites it
+          const unsigned accum = (k == 0 && i == 0 && j == w) ? 0u : 1u;
+          asm volatile(
+              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+              "l"(da), "l"(db), "r"(idesc), "r"(accum));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(&mbar[st])));
+    }
+    // step k + stages - 1 goes into the stage of step k - 1 once the MMAs of step k - 1 are done
+    const int kn = k + kTcStages - 1;
+    if (k >= 1 && kn < nk) {
+      const int kp = k - 1;
+      if (!mbar_wait(&mbar[kp % kTcStages], (kp / kTcStages) & 1)) ok = false;
+    }
+    if (ok) load_step(kn);
+    else cp_async_commit();
+    if (!ok) abort_sh = 1;
+    __syncthreads();
+    if (abort_sh) ok = false;
+  }
+  if (ok) {
+    const int last = nk - 1;
+    if (!mbar_wait(&mbar[last % kTcStages], (last / kTcStages) & 1)) ok = false;
+  }
+  cp_async_wait<0>();
+  if (!ok) {
+    if (tid == 0) atomicExch(&g_split_error, 1);
+    mbar_wait(&mbar[0], 0);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    const int row = tile.m0 + warp * 32 + lane;  // accumulator row = tensor-memory lane
+    const bool row_ok = row < a.M;
+    const int era = row_ok ? ea[row] : 0;
+#pragma unroll 1
+    for (int cb = 0; cb < kTcN / 16; ++cb) {
+      if (cb * 16 >= tile.ncol) break;
+      float v[kAcc][16];
+#pragma unroll
+      for (int w = 0; w < kAcc; ++w) {
+        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(w * kTcN + cb * 16);
+        unsigned r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[w][c] = __uint_as_float(r[c]);
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+      if (row_ok) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int col = cb * 16 + c;
+          if (col >= tile.ncol) break;
+          float h = 0.f, l = 0.f;
+#pragma unroll
+          for (int w = 0; w < kAcc; ++w) df_add(h, l, v[w][c]);
+          const long long vid = a.src_vec[tile.col0 + col];
+          store_out(a, a.dst_off[tile.col0 + col], row, h, l, era + a.eb[vid]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(kTcCols));
+  }
+}
+
+size_t tc_smem_bytes(int S) { return (size_t)kTcStages * S * (kTcA + kTcB) * sizeof(slice_t); }
+
+// ------------------------------------------------------------------ reduction
 
 // Reduction of double-float slots: y[dst] = sum of slots (double-float), written as FP64.
 __global__ void k_reduce_df(DFReduceArgs a) {
@@ -336,22 +523,21 @@ __global__ void k_reduce_df(DFReduceArgs a) {
   }
 }
 
-int kpad(int K) { return (K + kSKC - 1) / kSKC * kSKC; }
+constexpr int kKAlign = 32;  // padded K: a multiple of both engines' K steps
+int kpad(int K) { return (K + kKAlign - 1) / kKAlign * kKAlign; }
 
 int slice_table(const double* A, int nmat, int M, int K, int lda, long long mstride, int S, SplitTable* out,
                 cudaStream_t s) {
   out->M = M; out->K = K; out->Kpad = kpad(K); out->nmat = nmat;
   const size_t nh = (size_t)nmat * S * M * out->Kpad;
-  TRY(cudaMalloc(&out->A, nh * sizeof(__half)));
+  TRY(cudaMalloc(&out->A, nh * sizeof(slice_t)));
   TRY(cudaMalloc(&out->ea, (size_t)nmat * M * sizeof(int)));
   const long long rows = (long long)nmat * M;
   k_slice_rows<kSplitSlices><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(A, mstride, lda, M, K, out->Kpad,
-                                                                                 nmat, (__half*)out->A, out->ea);
+                                                                                 nmat, (slice_t*)out->A, out->ea);
   TRY(cudaGetLastError());
   return VP_OK;
 }
-
-size_t split_smem_bytes(int S) { return (size_t)2 * S * (kSBM + kSBN) * kSPitch * sizeof(__half); }
 
 }  // namespace
 
@@ -362,6 +548,7 @@ int build_split(vp_tables_s* T, cudaStream_t s) {
   if (!st) return VP_ERR_OOM;
   T->near_split = st;
   const int n = T->n, C = T->C, E = T->E, nl = T->levels + 1;
+  if (n > kSplitKMax || E > kSplitKMax || 2 * C > kSplitKMax) return VP_ERR_ARG;
   int rc;
   if ((rc = slice_table(T->near, nl * kNearPos, 3 * n, n, n, (long long)3 * n * n, S, &st->near, s))) return rc;
   if ((rc = slice_table(T->s2m, nl, E, n, n, (long long)E * n, S, &st->s2m, s))) return rc;
@@ -369,7 +556,9 @@ int build_split(vp_tables_s* T, cudaStream_t s) {
   if ((rc = slice_table(T->m2l, nl * kVOff * T->nch, C, C, C, (long long)C * C, S, &st->m2l, s))) return rc;
   if ((rc = slice_table(T->m2t, nl * kWPos * T->nch, 3 * n, C, C, (long long)3 * n * C, S, &st->m2t, s))) return rc;
   if ((rc = slice_table(T->s2l, nl * kXPos * T->nch, C, n, n, (long long)C * n, S, &st->s2l, s))) return rc;
-  if ((rc = slice_table(T->m2m, nl * T->nch, C, 4 * C, 4 * C, (long long)C * 4 * C, S, &st->m2m, s))) return rc;
+  if ((rc = slice_table(T->m2m, nl * T->nch, C, 2 * C, 4 * C, (long long)C * 4 * C, S, &st->m2m_lo, s))) return rc;
+  if ((rc = slice_table(T->m2m + 2 * C, nl * T->nch, C, 2 * C, 4 * C, (long long)C * 4 * C, S, &st->m2m_hi, s)))
+    return rc;
   if ((rc = slice_table(T->l2l, nl * 4 * T->nch, C, C, C, (long long)C * C, S, &st->l2l, s))) return rc;
   TRY(cudaStreamSynchronize(s));
   return VP_OK;
@@ -378,7 +567,8 @@ int build_split(vp_tables_s* T, cudaStream_t s) {
 void free_split_tables(vp_tables_s* T) {
   auto* st = static_cast<SplitTables*>(T->near_split);
   if (!st) return;
-  for (SplitTable* t : {&st->near, &st->s2m, &st->l2t, &st->m2l, &st->m2t, &st->s2l, &st->m2m, &st->l2l}) {
+  for (SplitTable* t : {&st->near, &st->s2m, &st->l2t, &st->m2l, &st->m2t, &st->s2l, &st->m2m_lo, &st->m2m_hi,
+                        &st->l2l}) {
     if (t->A) cudaFree(t->A);
     if (t->ea) cudaFree(t->ea);
   }
@@ -386,20 +576,30 @@ void free_split_tables(vp_tables_s* T) {
   T->near_split = nullptr;
 }
 
-// Per device: allow the GEMM kernel its dynamic shared memory (call outside stream capture).
+// Per device: allow the GEMM kernels their dynamic shared memory (call outside stream capture).
 int prepare_split_launch() {
   int dev = 0;
   TRY(cudaGetDevice(&dev));
   static bool done[64] = {false};
   if (dev >= 0 && dev < 64 && done[dev]) return VP_OK;
   TRY(cudaFuncSetAttribute(k_split_gemm<kSplitSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)split_smem_bytes(kSplitSlices)));
+                           (int)mma_smem_bytes(kSplitSlices)));
+  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes(kSplitSlices)));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return VP_OK;
 }
 
-int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s) {
-  const size_t smem = split_smem_bytes(kSplitSlices);
+int read_split_error(int* flag) {
+  int h = 0;
+  TRY(cudaMemcpyFromSymbol(&h, g_split_error, sizeof(int)));
+  const int zero = 0;
+  TRY(cudaMemcpyToSymbol(g_split_error, &zero, sizeof(int)));
+  *flag = h;
+  return VP_OK;
+}
+
+int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engine) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   TRY(cudaStreamIsCapturing(s, &cs));
   if (cs == cudaStreamCaptureStatusNone) {
@@ -407,7 +607,10 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s) {
     if (rc) return rc;
   }
   if (n_tiles <= 0) return VP_OK;
-  k_split_gemm<kSplitSlices><<<n_tiles, 256, smem, s>>>(a);
+  if (engine == kEngineTcgen05)
+    k_split_gemm_tc<kSplitSlices><<<n_tiles, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(a);
+  else
+    k_split_gemm<kSplitSlices><<<n_tiles, 256, mma_smem_bytes(kSplitSlices), s>>>(a);
   TRY(cudaGetLastError());
   return VP_OK;
 }
@@ -416,7 +619,7 @@ int launch_slice_list(const double* X, const long long* base, const long long* v
                       long long seg_stride, long long cstride, void* out, int* eb, cudaStream_t s) {
   if (nlist <= 0) return VP_OK;
   k_slice_list<kSplitSlices><<<(unsigned)((nlist * 32 + 255) / 256), 256, 0, s>>>(
-      X, base, vid, nlist, K, kseg > 0 ? kseg : K, seg_stride, cstride, kpad(K), (__half*)out, eb);
+      X, base, vid, nlist, K, kseg > 0 ? kseg : K, seg_stride, cstride, kpad(K), (slice_t*)out, eb);
   TRY(cudaGetLastError());
   return VP_OK;
 }

@@ -1,7 +1,7 @@
 // Split-precision (sliced operand) contractions: shared declarations.
 #pragma once
 
-#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -11,30 +11,35 @@ struct vp_tables_s;
 namespace vp {
 
 constexpr int kSplitSlices = 6;  // 8-bit slices per operand: about 48 significant bits each
+constexpr int kSplitKMax = 256;  // K of one contraction (exact fp32 sums need K * 2^16 <= 2^24)
+
+typedef __nv_bfloat16 slice_t;
 
 struct SplitTile {
   int group, m0, col0, ncol;
 };
 
-// One sliced operator family: slices [nmat][S][M][Kpad] (fp16) and row exponents [nmat][M].
+// One sliced operator family: slices [nmat][S][M][Kpad] (bf16) and row exponents [nmat][M].
 struct SplitTable {
   void* A = nullptr;
   int* ea = nullptr;
   int M = 0, K = 0, Kpad = 0, nmat = 0;
 };
 
+// m2m_lo / m2m_hi: the multipole-to-multipole operator split by children (0-1 and 2-3) so that
+// every contraction has K = 2C <= 256.
 struct SplitTables {
-  SplitTable near, s2m, l2t, m2l, m2t, s2l, m2m, l2l;
+  SplitTable near, s2m, l2t, m2l, m2t, s2l, m2m_lo, m2m_hi, l2l;
 };
 
 struct SplitArgs {
-  int M, Kpad, out_mode;       // out_mode 0: double-float slot (float2), 1: FP64 overwrite, 2: FP64 accumulate
-  const __half* A;
+  int M, Kpad, out_mode;        // out_mode 0: double-float slot (float2), 1: FP64 overwrite, 2: FP64 accumulate
+  const slice_t* A;
   const int* ea;
-  const __half* B;              // sliced vectors [v][S][Kpad]
+  const slice_t* B;             // sliced vectors [v][S][Kpad]
   const int* eb;
   void* Y;
-  const SplitTile* tiles;
+  const SplitTile* tiles;       // tiles of the engine that runs
   const long long* a_mat;       // per group: matrix index
   const long long* src_vec;     // per column: vector index
   const long long* dst_off;     // per column: destination offset (elements of 8 bytes)
@@ -52,14 +57,20 @@ struct DFReduceArgs {
   double* g;
 };
 
+// GEMM engines for the sliced contraction: warp-level mma.sync, or tcgen05 with tensor memory.
+constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1;
+constexpr int kSplitBM = 128;                    // rows per tile (both engines)
+constexpr int kSplitBN[2] = {64, 128};           // columns per tile, by engine
+
 int build_split(vp_tables_s* T, cudaStream_t s);
 void free_split_tables(vp_tables_s* T);
 int prepare_split_launch();
-int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s);
+int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engine);
+// Read and clear the flag that a bounded wait of the tcgen05 engine gave up.
+int read_split_error(int* flag);
 int launch_slice_list(const double* X, const long long* base, const long long* vid, long long nlist, int K, int kseg,
                       long long seg_stride, long long cstride, void* out, int* eb, cudaStream_t s);
 int launch_reduce_df(const DFReduceArgs& a, int n_dst, cudaStream_t s);
 int split_kpad(int K);
-constexpr int kSplitBM = 128, kSplitBN = 48;
 
 }  // namespace vp

@@ -1,0 +1,77 @@
+"""The tcgen05 engine of the split-precision contractions against the mma.sync engine, the oracle, and the
+autotuner that chooses between them."""
+import numpy as np
+import pytest
+
+import paper_1908_07392_gb300 as V
+from paper_1908_07392_gb300 import inputs as I
+from gpu_util import TOL_SPLIT, oracle_eval, rel_err, sample_nodes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    V.load_library()
+
+
+def _both_engines(w):
+    import torch
+    vp = V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, precision=V.VP_PREC_SPLIT)
+    try:
+        f = torch.from_numpy(w.f).cuda()
+        out = []
+        for eng in (V.ENGINE_MMA_SYNC, V.ENGINE_TCGEN05):
+            V.vp_tree_set_engine(vp.tree, eng)
+            u, g = vp(f)
+            torch.cuda.synchronize()
+            V.vp_device_status()
+            out.append((u.cpu().numpy(), g.cpu().numpy()))
+        return out
+    finally:
+        vp.close()
+
+
+def test_tcgen05_matches_mma_sync_small():
+    w = I.small_gaussian_workload()
+    (u0, g0), (u1, g1) = _both_engines(w)
+    assert rel_err(u1, u0) < 1e-13 and rel_err(g1, g0) < 1e-13
+
+
+@pytest.mark.parametrize("kernel,alpha,p", [(1, 300.0, 16), (0, 30.0, 12), (1, 10.0, 8)])
+def test_tcgen05_adaptive_against_oracle(kernel, alpha, p):
+    rng = np.random.default_rng(200 + p)
+    tree = I.random_balanced_tree(rng, 25, 6, side=3.0, min_depth=2)
+    X, Y = I.node_coords(tree, p)
+    fn = I.gaussian_sum(rng.uniform(-0.8, 0.8, (4, 2)), rng.uniform(0.1, 0.4, 4), rng.uniform(-1, 1, 4))
+    w = I.Workload("rand", kernel, alpha, p, tree, fn(X, Y))
+    (u0, g0), (u1, g1) = _both_engines(w)
+    assert rel_err(u1, u0) < 1e-13 and rel_err(g1, g0) < 1e-13
+    idx = sample_nodes(w, 200, 9)
+    ou, oux, ouy = oracle_eval(w, idx)
+    errs = (rel_err(u1[idx], ou), rel_err(g1[0, idx], oux), rel_err(g1[1, idx], ouy))
+    assert max(errs) < TOL_SPLIT, errs
+
+
+def test_autotune_keeps_results_and_uses_the_cache(tmp_path):
+    import torch
+    w = I.small_gaussian_workload(depth=4, p=8)
+    vp = V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, precision=V.VP_PREC_SPLIT)
+    try:
+        f = torch.from_numpy(w.f).cuda()
+        u_ref, g_ref = vp(f)
+        u = torch.empty_like(u_ref); g = torch.empty_like(g_ref)
+        cache = str(tmp_path / "tune.txt")
+        n1 = V.vp_autotune(vp.tree, f, u, g, cache)
+        torch.cuda.synchronize()
+        assert rel_err(u.cpu().numpy(), u_ref.cpu().numpy()) < 1e-13
+        lines = open(cache).read().strip().splitlines()
+        assert len(lines) > 0
+        n2 = V.vp_autotune(vp.tree, f, u, g, cache)   # second call reads the cache
+        assert n1 == n2
+        assert open(cache).read().strip().splitlines() == lines
+    finally:
+        vp.close()
