@@ -59,6 +59,27 @@ def load_library():
     lib.vp_tables_free.restype = None
     lib.vp_strerror.argtypes = [c_int]
     lib.vp_strerror.restype = ctypes.c_char_p
+    vpp = ctypes.POINTER(c_void_p)
+    lib.bie_create.argtypes = [c_double, c_double, c_double, c_int, c_double, c_int, c_int, c_void_p, vpp]
+    lib.bie_free.argtypes = [c_void_p]
+    lib.bie_free.restype = None
+    lib.bie_size.argtypes = [c_void_p, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]
+    lib.bie_nodes.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.bie_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.bie_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, ctypes.POINTER(c_int),
+                              ctypes.POINTER(c_double), c_void_p]
+    lib.bie_eval.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    lib.bie_stokeslets.argtypes = [c_double, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    lib.bie_kernel_scalars.argtypes = [c_int, c_void_p, c_void_p, c_void_p]
+    lib.ws_create.argtypes = [c_int, c_int, c_int, c_int, c_int, c_int, c_int, ctypes.c_uint64, c_void_p, vpp]
+    lib.ws_free.argtypes = [c_void_p]
+    lib.ws_free.restype = None
+    lib.ws_num_params.argtypes = [c_void_p, i64p]
+    lib.ws_params.argtypes = [c_void_p, c_void_p, c_int, c_void_p]
+    lib.ws_forward.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p]
+    lib.ws_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_void_p, ctypes.POINTER(ctypes.c_float), c_void_p]
+    lib.ws_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float,
+                                  ctypes.POINTER(ctypes.c_float), c_void_p]
     lib.vp_tree_set_engine.argtypes = [c_void_p, c_int]
     lib.vp_autotune.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_char_p, c_void_p,
                                 ctypes.POINTER(c_int)]
@@ -84,7 +105,10 @@ def exported_symbols():
     return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_eval", "vp_eval_host",
             "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
-            "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status"]
+            "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status",
+            "bie_create", "bie_free", "bie_size", "bie_nodes", "bie_apply", "bie_solve", "bie_eval",
+            "bie_stokeslets", "bie_kernel_scalars", "ws_create", "ws_free", "ws_num_params", "ws_params",
+            "ws_forward", "ws_grad", "ws_train_step"]
 
 
 ENGINE_MMA_SYNC = 0
@@ -305,6 +329,139 @@ class VolumePotential:
         if getattr(self, "tables", None):
             vp_tables_free(self.tables)
             self.tables = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------- boundary integral equation
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class BIE:
+    """Nystrom discretisation of 1/2 mu + D[mu] + W[mu] = g on a star boundary, solved by GMRES on the GPU."""
+
+    def __init__(self, alpha, R=1.0, A=0.3, k=5, phase=0.0, n_panels=256, max_krylov=300, stream=None):
+        import torch
+        out = ctypes.c_void_p()
+        _check(load_library().bie_create(float(alpha), float(R), float(A), int(k), float(phase), int(n_panels),
+                                         int(max_krylov), _stream_ptr(stream), ctypes.byref(out)), "bie_create")
+        self.handle = out.value
+        n = ctypes.c_int(); L = ctypes.c_double()
+        _check(load_library().bie_size(ctypes.c_void_p(self.handle), ctypes.byref(n), ctypes.byref(L)), "bie_size")
+        self.N, self.length, self.alpha = n.value, L.value, alpha
+        self.max_krylov = max_krylov
+        nodes = torch.empty(7, self.N, dtype=torch.float64, device="cuda")
+        _check(load_library().bie_nodes(ctypes.c_void_p(self.handle), _p(nodes), _stream_ptr(stream)), "bie_nodes")
+        self.nodes = nodes   # x, y, nx, ny, w, kappa, t
+
+    def apply(self, mu, out=None, stream=None):
+        import torch
+        out = torch.empty_like(mu) if out is None else out
+        _check(load_library().bie_apply(ctypes.c_void_p(self.handle), _p(mu), _p(out), _stream_ptr(stream)), "bie_apply")
+        return out
+
+    def solve(self, g, mu0=None, tol=1e-11, max_iter=None, stream=None):
+        """Returns (mu, iterations, true relative residual); mu0 is the initial guess (zeros if None)."""
+        import torch
+        mu = torch.zeros_like(g) if mu0 is None else mu0.clone()
+        it = ctypes.c_int(); rr = ctypes.c_double()
+        _check(load_library().bie_solve(ctypes.c_void_p(self.handle), _p(g), _p(mu), float(tol),
+                                        int(max_iter or self.max_krylov), ctypes.byref(it), ctypes.byref(rr),
+                                        _stream_ptr(stream)), "bie_solve")
+        return mu, it.value, rr.value
+
+    def eval(self, mu, txy, stream=None):
+        import torch
+        M = txy.shape[1]
+        u = torch.empty(2, M, dtype=torch.float64, device="cuda")
+        _check(load_library().bie_eval(ctypes.c_void_p(self.handle), _p(mu), int(M), _p(txy), _p(u),
+                                       _stream_ptr(stream)), "bie_eval")
+        return u
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().bie_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bie_stokeslets(alpha, src, f, xy, stream=None):
+    """u [2][M] of stokeslets at src [K][2] with strengths f [K][2] (device float64 tensors) at xy [2][M]."""
+    import torch
+    M = xy.shape[1]
+    u = torch.empty(2, M, dtype=torch.float64, device="cuda")
+    _check(load_library().bie_stokeslets(float(alpha), int(src.shape[0]), _p(src), _p(f), int(M), _p(xy), _p(u),
+                                         _stream_ptr(stream)), "bie_stokeslets")
+    return u
+
+
+def bie_kernel_scalars(z, stream=None):
+    """T1, T2, T3, S1, S2 of the stresslet and stokeslet at z (device float64) -> [5][n]."""
+    import torch
+    out = torch.empty(5, z.numel(), dtype=torch.float64, device="cuda")
+    _check(load_library().bie_kernel_scalars(int(z.numel()), _p(z), _p(out), _stream_ptr(stream)),
+           "bie_kernel_scalars")
+    return out
+
+
+class WarmStartNet:
+    """Circular 1D conv net over boundary nodes (FP32), hand-written CUDA forward/backward/Adam."""
+
+    def __init__(self, in_ch=8, width=64, out_ch=2, n_layers=4, ksize=9, n=4096, max_batch=32, seed=5, stream=None):
+        out = ctypes.c_void_p()
+        _check(load_library().ws_create(in_ch, width, out_ch, n_layers, ksize, n, max_batch, ctypes.c_uint64(seed),
+                                        _stream_ptr(stream), ctypes.byref(out)), "ws_create")
+        self.handle = out.value
+        cnt = ctypes.c_int64()
+        _check(load_library().ws_num_params(ctypes.c_void_p(self.handle), ctypes.byref(cnt)), "ws_num_params")
+        self.n_params = cnt.value
+        self.in_ch, self.out_ch, self.n, self.max_batch = in_ch, out_ch, n, max_batch
+
+    def params(self):
+        import torch
+        buf = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(load_library().ws_params(ctypes.c_void_p(self.handle), _p(buf), 1, _stream_ptr(None)), "ws_params")
+        return buf
+
+    def set_params(self, buf):
+        _check(load_library().ws_params(ctypes.c_void_p(self.handle), _p(buf), 0, _stream_ptr(None)), "ws_params")
+
+    def forward(self, x):
+        import torch
+        y = torch.empty(x.shape[0], self.out_ch, self.n, dtype=torch.float32, device="cuda")
+        _check(load_library().ws_forward(ctypes.c_void_p(self.handle), _p(x), int(x.shape[0]), _p(y),
+                                         _stream_ptr(None)), "ws_forward")
+        return y
+
+    def grad(self, x, t):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        loss = ctypes.c_float()
+        _check(load_library().ws_grad(ctypes.c_void_p(self.handle), _p(x), _p(t), int(x.shape[0]), _p(g),
+                                      ctypes.byref(loss), _stream_ptr(None)), "ws_grad")
+        return g, loss.value
+
+    def train_step(self, x, t, lr):
+        loss = ctypes.c_float()
+        _check(load_library().ws_train_step(ctypes.c_void_p(self.handle), _p(x), _p(t), int(x.shape[0]), float(lr),
+                                            ctypes.byref(loss), _stream_ptr(None)), "ws_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().ws_free(ctypes.c_void_p(self.handle))
+            self.handle = None
 
     def __del__(self):
         try:

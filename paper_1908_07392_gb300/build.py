@@ -10,9 +10,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["tables.cu", "eval.cu", "split.cu"]
+CU_SOURCES = ["tables.cu", "eval.cu", "split.cu", "bie.cu", "ws.cu"]
 CPP_SOURCES = ["plan.cpp"]
-HEADERS = ["special.cuh", "vp_internal.h", "plan.h", "split.h", os.path.join("..", "..", "include", "vp.h")]
+HEADERS = ["special.cuh", "vp_internal.h", "plan.h", "split.h", os.path.join("..", "..", "include", "vp.h"),
+           os.path.join("..", "..", "include", "bie.h")]
 
 
 def _nvcc():

@@ -650,7 +650,6 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
       if (rc) return rc;
     } else if (st.kind == 4) {
       const DevSplit& d = tr->splits[st.index];
-      const SplitTables* stt = static_cast<const SplitTables*>(T->near_split);
       SplitArgs a = split_args(tr, d, bufs);
       const int rc = launch_split_gemm(a, d.n_tiles[d.engine], s, d.engine);
       if (rc) return rc;
@@ -836,9 +835,7 @@ int time_split_launches(vp_tree_s* tr, const double* f, double* u, double* g, in
   std::vector<cudaEvent_t> ev(2 * ns, nullptr);
   for (auto& x : ev) if (cudaEventCreate(&x) != cudaSuccess) return VP_ERR_CUDA;
   int rc = run_steps(tr, f, u, g, s);  // warm up
-  const double* bufs_c[BUF_COUNT] = {f, tr->mp, tr->loc, tr->lslot, tr->uslot};
   double* bufs[BUF_COUNT] = {nullptr, tr->mp, tr->loc, tr->lslot, tr->uslot};
-  (void)bufs_c;
   for (int k = 0; rc == VP_OK && k < ns; ++k) {
     DevSplit d = tr->splits[k];
     d.engine = engine;

@@ -346,8 +346,8 @@ __device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity) {
 
 template <int S>
 __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  slice_t* As = reinterpret_cast<slice_t*>(smem_raw);  // [stages][S][kTcA]
+  extern __shared__ __align__(16) unsigned char smem_tc[];
+  slice_t* As = reinterpret_cast<slice_t*>(smem_tc);  // [stages][S][kTcA]
   slice_t* Bs = As + kTcStages * S * kTcA;              // [stages][S][kTcB]
   __shared__ __align__(8) unsigned long long mbar[kTcStages];
   __shared__ unsigned tmem_base_sh;

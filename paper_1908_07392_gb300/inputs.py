@@ -324,3 +324,24 @@ def batched_workloads(seed=4, n_trees=64, nmin=1e4, nmax=5e5, amin=10.0, amax=10
         X, Y = node_coords(tree, p)
         out.append(Workload(f"batch{k}_p{p}_a{alpha:.1f}", KERNEL_MHELMHOLTZ, alpha, p, tree, fn(X, Y), fn))
     return out
+
+
+def moving_stokeslets(seed=5, n_sources=5, radius=(1.6, 2.1)):
+    """Seeded exterior forcing for a sequence of boundary-value problems: stokeslets on circles
+    outside the star (radius 1.6..2.1 > 1.3), each rotating with its own angular speed, with
+    strengths oscillating in time. Returns a function t -> (sources [K][2], strengths [K][2])."""
+    rng = np.random.default_rng(seed)
+    rad = rng.uniform(radius[0], radius[1], n_sources)
+    ang0 = rng.uniform(0, 2 * np.pi, n_sources)
+    om = rng.uniform(-2.0, 2.0, n_sources)
+    f0 = rng.uniform(-1, 1, (n_sources, 2))
+    f1 = rng.uniform(-0.5, 0.5, (n_sources, 2))
+    nu = rng.uniform(1.0, 4.0, (n_sources, 2))
+    ph = rng.uniform(0, 2 * np.pi, (n_sources, 2))
+
+    def at(t):
+        a = ang0 + om * t
+        src = np.stack([rad * np.cos(a), rad * np.sin(a)], axis=1)
+        f = f0 + f1 * np.sin(nu * t + ph)
+        return src, f
+    return at

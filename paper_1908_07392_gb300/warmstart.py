@@ -1,0 +1,143 @@
+"""Learned warm start for the per-step boundary integral equation.
+
+A sequence of steps n = 0, 1, ... each solves (1/2 + D + W) mu_n = g_n by GMRES (library). The
+network (library kernels) sees the last three densities and the current boundary data, all scaled
+by fixed factors, and predicts the correction to the cubic extrapolation 3 mu_{n-1} - 3 mu_{n-2}
++ mu_{n-3}; its output, scaled back and added to that extrapolation, is the initial guess. It is
+trained on densities that plain (cold-start) GMRES solves produce. Plain GMRES to the same residual
+stays the solver and the judge of the result: the guess only changes where GMRES starts.
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import BIE, WarmStartNet, bie_stokeslets
+from . import inputs as I
+
+
+def boundary_data(bie, forcing, times):
+    """g_n at the boundary nodes for each time (device, [steps][2N] interleaved per node)."""
+    import torch
+    xy = bie.nodes[0:2].contiguous()
+    out = []
+    for t in times:
+        src, f = forcing(t)
+        u = bie_stokeslets(bie.alpha, torch.tensor(src, device="cuda"), torch.tensor(f, device="cuda"), xy)
+        out.append(u.t().contiguous().reshape(-1))    # (x, y) per node
+    return torch.stack(out)
+
+
+def plain_solves(bie, G, tol):
+    import torch
+    mus, its = [], []
+    for g in G:
+        mu, it, rr = bie.solve(g, None, tol)
+        if not rr <= 10 * tol:
+            raise RuntimeError(f"GMRES did not reach the tolerance ({rr:.2e})")
+        mus.append(mu); its.append(it)
+    return torch.stack(mus), its
+
+
+def _features(mus, G, n, s_mu, s_g):
+    """Network inputs [B][8][N] and the cubic extrapolation [B][2N] for steps n (index array)."""
+    import torch
+    N = mus.shape[1] // 2
+    ch = []
+    for lag in (1, 2, 3):
+        ch.append(mus[n - lag].reshape(-1, N, 2).permute(0, 2, 1) / s_mu)
+    ch.append(G[n].reshape(-1, N, 2).permute(0, 2, 1) / s_g)
+    x = torch.cat(ch, dim=1).float().contiguous()
+    ext = 3 * mus[n - 1] - 3 * mus[n - 2] + mus[n - 3]
+    return x, ext
+
+
+def train(net, mus, G, train_idx, epochs=40, batch=16, lr=1e-3, seed=0):
+    import torch
+    s_mu = float(mus.std()) or 1.0
+    s_g = float(G.std()) or 1.0
+    N = mus.shape[1] // 2
+    err = mus[train_idx] - (3 * mus[train_idx - 1] - 3 * mus[train_idx - 2] + mus[train_idx - 3])
+    s_err = float(err.std()) or 1.0
+    rng = np.random.default_rng(seed)
+    losses = []
+    for ep in range(epochs):
+        order = rng.permutation(train_idx)
+        for k in range(0, len(order) - batch + 1, batch):
+            n = torch.tensor(order[k:k + batch], device="cuda")
+            x, ext = _features(mus, G, n, s_mu, s_g)
+            t = ((mus[n] - ext).reshape(-1, N, 2).permute(0, 2, 1) / s_err).float().contiguous()
+            losses.append(net.train_step(x, t, lr))
+    return {"s_mu": s_mu, "s_g": s_g, "s_err": s_err, "losses": losses}
+
+
+def guess(net, scale, mus, G, n):
+    import torch
+    N = mus.shape[1] // 2
+    idx = torch.tensor([n], device="cuda")
+    x, ext = _features(mus, G, idx, scale["s_mu"], scale["s_g"])
+    y = net.forward(x)[0]                                   # [2][N]
+    return ext[0] + scale["s_err"] * y.permute(1, 0).reshape(-1).double()
+
+
+def evaluate(bie, net, scale, mus, G, test_idx, tol):
+    """GMRES iterations and solve times from each initial guess on the held-out steps."""
+    import torch
+    res = {k: {"iters": [], "ms": []} for k in ("cold", "previous", "extrapolation", "network")}
+    for n in test_idx:
+        g = G[n]
+        guesses = {
+            "cold": None,
+            "previous": mus[n - 1],
+            "extrapolation": 3 * mus[n - 1] - 3 * mus[n - 2] + mus[n - 3],
+        }
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        guesses["network"] = guess(net, scale, mus, G, n)
+        torch.cuda.synchronize()
+        t_net = time.perf_counter() - t0
+        for k, x0 in guesses.items():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mu, it, rr = bie.solve(g, x0, tol)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0 + (t_net if k == "network" else 0.0)
+            if not rr <= 10 * tol:
+                raise RuntimeError(f"GMRES from the {k} guess did not reach the tolerance ({rr:.2e})")
+            res[k]["iters"].append(it)
+            res[k]["ms"].append(1000 * dt)
+    return {k: {"mean_iters": float(np.mean(v["iters"])), "max_iters": int(np.max(v["iters"])),
+                "mean_ms": float(np.mean(v["ms"]))} for k, v in res.items()}
+
+
+def experiment(alpha, n_panels=256, n_train=2000, n_test=200, dt=1e-3, tol=1e-11, epochs=40, batch=16,
+               lr=1e-3, seed=5, width=64, n_layers=4, ksize=9):
+    """Plain solves for n_train + n_test + 3 steps of a star with moving exterior forcing, network
+    training on the first n_train, iterations and times from each initial guess on the rest."""
+    rng = np.random.default_rng(seed)
+    bie = BIE(alpha, R=1.0, A=0.3, k=5, phase=float(rng.uniform(0, 2 * np.pi)), n_panels=n_panels, max_krylov=300)
+    try:
+        forcing = I.moving_stokeslets(seed)
+        steps = n_train + n_test + 3
+        times = dt * np.arange(steps)
+        t0 = time.perf_counter()
+        G = boundary_data(bie, forcing, times)
+        mus, its = plain_solves(bie, G, tol)
+        t_plain = time.perf_counter() - t0
+        net = WarmStartNet(in_ch=8, width=width, out_ch=2, n_layers=n_layers, ksize=ksize, n=bie.N,
+                           max_batch=batch, seed=seed)
+        try:
+            t0 = time.perf_counter()
+            scale = train(net, mus, G, np.arange(3, 3 + n_train), epochs=epochs, batch=batch, lr=lr, seed=seed)
+            t_train = time.perf_counter() - t0
+            test_idx = np.arange(3 + n_train, steps)
+            ev = evaluate(bie, net, scale, mus, G, test_idx, tol)
+        finally:
+            net.close()
+        return {"nodes": bie.N, "alpha": alpha, "n_train": n_train, "n_test": n_test, "tol": tol,
+                "plain_mean_iters": float(np.mean(its)), "plain_seconds": t_plain, "train_seconds": t_train,
+                "final_train_loss": float(np.mean(scale["losses"][-20:])), "first_train_loss": float(scale["losses"][0]),
+                "held_out": ev}
+    finally:
+        bie.close()

@@ -19,9 +19,12 @@ def lib():
 
 
 def header_functions():
-    text = open(os.path.join(ROOT, "include", "vp.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(vp_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    for h in ("vp.h", "bie.h"):
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b((?:vp|bie|ws)_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_library_exports_every_declared_symbol(lib):
