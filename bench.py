@@ -49,8 +49,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--max-depth", type=int, default=10, help="tree depth cap (10 = the stated workload)")
-    ap.add_argument("--workload", default="star", choices=["star", "batched"],
-                    help="star: one adaptive tree (default); batched: 64 trees in one CUDA graph")
+    ap.add_argument("--workload", default="star", choices=["star", "batched", "steps"],
+                    help="star: one adaptive tree (default); batched: 64 trees in one CUDA graph; "
+                         "steps: coupled volume potential + boundary solve with the learned warm start")
+    ap.add_argument("--train-steps", type=int, default=2000, help="steps workload: plain solves to train on")
+    ap.add_argument("--test-steps", type=int, default=200, help="steps workload: held-out steps")
+    ap.add_argument("--epochs", type=int, default=40, help="steps workload: training epochs")
     ap.add_argument("--streams", type=int, default=16, help="graph branches for the batched workload")
     ap.add_argument("--engine", default="auto", choices=["auto", "mma", "tcgen05"],
                     help="split-precision GEMM engine: autotuned per launch, mma.sync, or tcgen05")
@@ -280,6 +284,54 @@ def run_batched(args):
         vp.close()
 
 
+def run_steps(args):
+    """Coupled steps in the star (Re = 100, dt = 1e-3, alpha = sqrt(Re/dt)): per step the volume
+    potential of the vorticity source on a uniform depth-7, p = 16 tree (4.19M nodes), its boundary
+    trace, and GMRES (tol 1e-11) for 256 panels x 16 nodes from a cold, previous, extrapolated or
+    network initial guess; the network is trained on the plain solves of the first steps."""
+    import numpy as np
+    import torch
+    import paper_1908_07392_gb300 as V
+    from paper_1908_07392_gb300 import build as B
+    from paper_1908_07392_gb300 import inputs as I
+    from paper_1908_07392_gb300 import warmstart as WS
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    B.build()
+    wl = I.step_workload(seed=5 + rank)
+    prec = V.VP_PREC_SPLIT if args.precision == "split" else V.VP_PREC_FP64
+    log = (lambda m: print(m, file=sys.stderr, flush=True)) if rank == 0 else None
+    t0 = time.perf_counter()
+    sampler = ClockSampler(local)
+    with sampler:
+        r = WS.step_experiment(wl, n_panels=256, n_train=args.train_steps, n_test=args.test_steps, tol=1e-11,
+                               precision=prec, epochs=args.epochs, log=log)
+    wall = time.perf_counter() - t0
+    b = V.BIE(wl.alpha, R=1.0, A=0.3, k=5, phase=wl.phi, n_panels=256)
+    try:
+        err, _ = WS.interior_error(b, wl.boundary, 0.0)
+    finally:
+        b.close()
+    ev = r["held_out"]
+    line = {"metric": "coupled step time with the learned GMRES warm start", "value": ev["network"]["mean_ms"],
+            "unit": "ms/step", "n_gpus": world, "steps": args.test_steps, "warmup": 3 + args.train_steps,
+            "ms_per_step": ev["network"]["mean_ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 solve, f32 network", "data": "synthetic",
+            "config": {"workload": wl.name, "alpha": wl.alpha, "boundary_nodes": r["nodes"],
+                       "volume_nodes": r["volume_nodes"], "volume_precision": args.precision,
+                       "train_steps": args.train_steps, "test_steps": args.test_steps, "epochs": args.epochs,
+                       "gmres_tol": 1e-11, "net": "circular conv1d 8-64-64-64-2, kernel 9, fp32"},
+            "held_out": ev,
+            "iterations_saved_vs_cold": ev["cold"]["mean_iters"] - ev["network"]["mean_iters"],
+            "iterations_saved_vs_extrapolation": ev["extrapolation"]["mean_iters"] - ev["network"]["mean_iters"],
+            "plain_mean_iters": r["plain_mean_iters"], "volume_ms_mean": r["volume_ms_mean"],
+            "train_seconds": r["train_seconds"], "train_loss": [r["first_train_loss"], r["final_train_loss"]],
+            "interior_rel_err_exact_solution": err, "wall_seconds": wall,
+            "clocks": sampler.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -287,6 +339,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "steps":
+        run_steps(args)
         return
     import torch
     import paper_1908_07392_gb300 as V

@@ -133,6 +133,21 @@ int vp_tree_size(vp_tree tree, int64_t* n_leaves, int64_t* n_nodes);
 int vp_tree_nodes(vp_tree tree, double* xy, void* stream);
 
 /*
+ * vp_tree_interp -- evaluate nodal fields off the grid through each leaf's tensor Lagrange
+ * interpolant on its p x p Gauss-Legendre nodes (the same leaf polynomial that represents f in
+ * Eq. vol_pot, Sec. 3.1). Used to carry a volume potential to boundary nodes (Sec. 2.2: the
+ * boundary data of the homogeneous problem is the boundary condition minus the particular solution).
+ *  fields  device [n_fields][N] nodal values in node order (e.g. gradu of vp_eval, n_fields = 2).
+ *  xy      device [2][M] points; out device [n_fields][M].
+ * A point on a leaf edge takes either adjacent leaf. Points outside the root box get NaN.
+ * The first call on a tree allocates and fills a cell-to-leaf map of 4^L ints (L = deepest leaf
+ * level; not inside graph capture). Errors: VP_ERR_ARG, VP_ERR_LEVELS (L > 13), VP_ERR_OOM,
+ * VP_ERR_CUDA.
+ */
+int vp_tree_interp(vp_tree tree, int n_fields, const double* fields, int n_points, const double* xy, double* out,
+                   void* stream);
+
+/*
  * vp_eval -- the volume potential and its gradient at every node.
  *  f      device [N] nodal source values (read only).
  *  u      device [N] output.

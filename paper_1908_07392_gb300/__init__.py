@@ -51,6 +51,7 @@ def load_library():
                                    ctypes.POINTER(c_void_p)]
     lib.vp_tree_size.argtypes = [c_void_p, i64p, i64p]
     lib.vp_tree_nodes.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.vp_tree_interp.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     lib.vp_eval.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.vp_eval_host.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.vp_tree_free.argtypes = [c_void_p]
@@ -102,7 +103,7 @@ def load_library():
 
 def exported_symbols():
     """Names declared in include/vp.h (the ABI surface)."""
-    return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_eval", "vp_eval_host",
+    return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_tree_interp", "vp_eval", "vp_eval_host",
             "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
             "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status",
@@ -187,6 +188,13 @@ def vp_tree_size(tree: int):
 def vp_tree_nodes(tree: int, xy, stream=None):
     _check(load_library().vp_tree_nodes(ctypes.c_void_p(tree), ctypes.c_void_p(xy.data_ptr()), _stream_ptr(stream)),
            "vp_tree_nodes")
+
+
+def vp_tree_interp(tree: int, fields, xy, out, stream=None):
+    """fields: device float64 [F, N]; xy: [2, M]; out: [F, M]."""
+    _check(load_library().vp_tree_interp(ctypes.c_void_p(tree), int(fields.shape[0]), ctypes.c_void_p(fields.data_ptr()),
+                                         int(xy.shape[1]), ctypes.c_void_p(xy.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "vp_tree_interp")
 
 
 def vp_eval(tree: int, f, u, gradu, stream=None):
@@ -312,6 +320,15 @@ class VolumePotential:
         xy = torch.empty(2, self.N, dtype=torch.float64, device=self.device)
         vp_tree_nodes(self.tree, xy)
         return xy
+
+    def interp(self, fields, xy):
+        """Leaf interpolants of fields [F, N] at points xy [2, M] -> [F, M]."""
+        import torch
+        fields = fields.reshape(-1, self.N).contiguous()
+        xy = xy.contiguous()
+        out = torch.empty(fields.shape[0], xy.shape[1], dtype=torch.float64, device=fields.device)
+        vp_tree_interp(self.tree, fields, xy, out)
+        return out
 
     def __call__(self, f, u=None, gradu=None):
         import torch

@@ -54,6 +54,9 @@ struct GemmArgs {
 // are contiguous, so a half-warp stores 16 consecutive doubles.
 constexpr int kBM = 64, kBN = 64, kBK = 16;
 
+// Deepest leaf level vp_tree_interp serves (its cell map holds 4^L ints: 256 MB at L = 13).
+constexpr int kInterpMaxLevel = 13;
+
 // TAG only names the instantiation (1: near-field tables) so profilers can pick it out.
 template <int TAG>
 __global__ void __launch_bounds__(256) k_gemm_gather_f64(GemmArgs a) {
@@ -159,6 +162,63 @@ __global__ void k_nodes(int p, int n_leaves, double x0, double y0, double side, 
   xy[N + i] = y0 + (iy[leaf] + 0.5 * (1.0 + xi[t / p])) * h;
 }
 
+// Cell map at the finest level L: the leaves tile the root box, so each of the 4^L cells is
+// covered by exactly one leaf, written by that leaf's block.
+__global__ void k_cell_map(int n_leaves, int L, const int* lv, const int* ix, const int* iy, int* cell) {
+  const int leaf = blockIdx.x;
+  if (leaf >= n_leaves) return;
+  const int sh = L - lv[leaf];
+  const long long w = 1ll << sh, dim = 1ll << L;
+  const long long x0 = (long long)ix[leaf] << sh, y0 = (long long)iy[leaf] << sh;
+  for (long long k = threadIdx.x; k < w * w; k += blockDim.x) cell[(y0 + k / w) * dim + x0 + k % w] = leaf;
+}
+
+// Lagrange basis on the p Gauss-Legendre nodes at t (product form; exact 0/1 at the nodes).
+__device__ inline void lagrange_basis(int p, const double* xi, double t, double* l) {
+  for (int i = 0; i < p; ++i) {
+    double v = 1.0;
+    for (int k = 0; k < p; ++k)
+      if (k != i) v *= (t - xi[k]) / (xi[i] - xi[k]);
+    l[i] = v;
+  }
+}
+
+// One thread per point: locate the leaf, evaluate the leaf's tensor interpolant of each field.
+__global__ void k_interp(int p, int L, double x0, double y0, double side, const int* lv, const int* ix,
+                        const int* iy, const double* xi_g, const int* cell, int n_fields, const double* F,
+                        long long N, int M, const double* pts, double* out) {
+  __shared__ double xi[16];
+  if (threadIdx.x < p) xi[threadIdx.x] = xi_g[threadIdx.x];
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const double px = pts[m], py = pts[(long long)M + m];
+  const long long dim = 1ll << L;
+  const double sx = (px - x0) / side * (double)dim, sy = (py - y0) / side * (double)dim;
+  if (!(sx >= 0.0 && sx <= (double)dim && sy >= 0.0 && sy <= (double)dim)) {
+    for (int f = 0; f < n_fields; ++f) out[(long long)f * M + m] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  const long long cx = min((long long)sx, dim - 1), cy = min((long long)sy, dim - 1);
+  const int leaf = cell[cy * dim + cx];
+  const double h = side / (double)(1ll << lv[leaf]);
+  const double tx = 2.0 * ((px - x0) / h - ix[leaf]) - 1.0, ty = 2.0 * ((py - y0) / h - iy[leaf]) - 1.0;
+  double lx[16], ly[16];
+  lagrange_basis(p, xi, tx, lx);
+  lagrange_basis(p, xi, ty, ly);
+  const long long base = (long long)leaf * p * p;
+  for (int f = 0; f < n_fields; ++f) {
+    const double* v = F + (long long)f * N + base;
+    double acc = 0.0;
+    for (int j = 0; j < p; ++j) {
+      double row = 0.0;
+      for (int i = 0; i < p; ++i) row = fma(lx[i], v[j * p + i], row);
+      acc = fma(ly[j], row, acc);
+    }
+    out[(long long)f * M + m] = acc;
+  }
+}
+
 // ----------------------------------------------------------------- host plan -> device ops
 
 struct HostGemm {
@@ -242,6 +302,8 @@ struct vp_tree_s {
   // host staging for vp_eval_host
   double *h_f = nullptr, *h_u = nullptr;
   double *d_f = nullptr, *d_u = nullptr, *d_g = nullptr;
+  // point location for vp_tree_interp: finest-level cell -> leaf, built on first use
+  int* d_cell = nullptr;
 };
 
 namespace vp {
@@ -723,6 +785,30 @@ extern "C" int vp_tree_nodes(vp_tree tree, double* xy, void* stream) {
   k_nodes<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(T->p, tree->n_leaves, tree->cx - 0.5 * T->side,
                                                      tree->cy - 0.5 * T->side, T->side, tree->d_lv, tree->d_ix,
                                                      tree->d_iy, tree->d_xi, N, xy);
+  TRY(cudaGetLastError());
+  return VP_OK;
+}
+
+extern "C" int vp_tree_interp(vp_tree tree, int n_fields, const double* fields, int n_points, const double* xy,
+                              double* out, void* stream) {
+  if (!tree || n_fields < 1 || n_points < 0 || (n_points > 0 && (!fields || !xy || !out))) return VP_ERR_ARG;
+  if (n_points == 0) return VP_OK;
+  if (tree->max_level > kInterpMaxLevel) return VP_ERR_LEVELS;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const vp_tables_s* T = tree->T;
+  if (!tree->d_cell) {
+    void* p = nullptr;
+    const size_t cells = (size_t)1 << (2 * tree->max_level);
+    TRY(cudaMalloc(&p, cells * sizeof(int)));
+    tree->allocs.push_back(p);
+    k_cell_map<<<tree->n_leaves, 256, 0, s>>>(tree->n_leaves, tree->max_level, tree->d_lv, tree->d_ix, tree->d_iy,
+                                             static_cast<int*>(p));
+    TRY(cudaGetLastError());
+    tree->d_cell = static_cast<int*>(p);
+  }
+  k_interp<<<(unsigned)((n_points + 127) / 128), 128, 0, s>>>(
+      T->p, tree->max_level, tree->cx - 0.5 * T->side, tree->cy - 0.5 * T->side, T->side, tree->d_lv, tree->d_ix,
+      tree->d_iy, tree->d_xi, tree->d_cell, n_fields, fields, tree->N, n_points, xy, out);
   TRY(cudaGetLastError());
   return VP_OK;
 }

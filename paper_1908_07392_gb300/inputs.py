@@ -345,3 +345,54 @@ def moving_stokeslets(seed=5, n_sources=5, radius=(1.6, 2.1)):
         f = f0 + f1 * np.sin(nu * t + ph)
         return src, f
     return at
+
+
+@dataclasses.dataclass
+class StepWorkload:
+    """A sequence of modified Stokes problems in the star r(t) = 1 + 0.3 cos(5t + phi) (one per
+    time step): a vorticity source on a uniform volume tree and a moving exterior forcing that sets
+    the boundary velocity."""
+    name: str
+    alpha: float
+    dt: float
+    p: int
+    tree: Tree
+    phi: float
+    source: Callable      # (X, Y, t) -> source values, torch tensors on any device
+    boundary: Callable    # t -> (stokeslet positions [K][2], strengths [K][2])
+
+
+def step_workload(seed=5, depth=7, p=16, re=100.0, dt=1e-3, n_gauss=3, blend=0.05, side=3.0) -> StepWorkload:
+    """Star domain of the star-source workload (phase seeded), alpha = sqrt(Re / dt) (about 316 at
+    Re = 100, dt = 1e-3), box [-1.5, 1.5]^2, uniform depth-7 tree with p = 16 (4.19M nodes).
+    Source: the smooth star field of the adaptive workload times the C-infinity radial blend,
+    plus n_gauss Gaussians (widths U[0.1, 0.3], amplitudes U[-1, 1]) whose centres rotate about
+    the origin at radius <= 0.56 (inside the star for every phase) with angular speeds U[-2, 2];
+    the background field drifts with t. Boundary forcing: moving_stokeslets(seed)."""
+    rng = np.random.default_rng(seed)
+    phi = float(rng.uniform(0.0, 2 * np.pi))
+    rad = np.sqrt(rng.uniform(0.0, 1.0, n_gauss)) * 0.56
+    ang0 = rng.uniform(0.0, 2 * np.pi, n_gauss)
+    om = rng.uniform(-2.0, 2.0, n_gauss)
+    widths = rng.uniform(0.1, 0.3, n_gauss)
+    amps = rng.uniform(-1.0, 1.0, n_gauss)
+
+    def source(X, Y, t):
+        import torch
+        r = torch.hypot(X, Y)
+        th = torch.atan2(Y, X)
+        s = (r - (1.0 + 0.3 * torch.cos(5 * th + phi))) / blend
+        a = torch.clamp(1.0 - s, 0.0, 1.0)
+        b = torch.clamp(s, 0.0, 1.0)
+        pa = torch.where(a > 0, torch.exp(-1.0 / torch.where(a > 0, a, torch.ones_like(a))), torch.zeros_like(a))
+        pb = torch.where(b > 0, torch.exp(-1.0 / torch.where(b > 0, b, torch.ones_like(b))), torch.zeros_like(b))
+        chi = pa / (pa + pb)
+        val = torch.cos(2 * X + 0.3 * t) * torch.sin(3 * Y - 0.2 * t) + 0.5
+        for k in range(n_gauss):
+            cx = rad[k] * math.cos(ang0[k] + om[k] * t)
+            cy = rad[k] * math.sin(ang0[k] + om[k] * t)
+            val = val + amps[k] * torch.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (widths[k] ** 2))
+        return chi * val
+
+    return StepWorkload(f"star_steps_uniform_d{depth}_p{p}_re{re:g}_dt{dt:g}", math.sqrt(re / dt), dt, p,
+                        uniform_tree(depth, side=side), phi, source, moving_stokeslets(seed))

@@ -13,7 +13,7 @@ import time
 
 import numpy as np
 
-from . import BIE, WarmStartNet, bie_stokeslets
+from . import BIE, VP_PREC_FP64, VolumePotential, WarmStartNet, bie_stokeslets
 from . import inputs as I
 
 
@@ -81,12 +81,13 @@ def guess(net, scale, mus, G, n):
     return ext[0] + scale["s_err"] * y.permute(1, 0).reshape(-1).double()
 
 
-def evaluate(bie, net, scale, mus, G, test_idx, tol):
-    """GMRES iterations and solve times from each initial guess on the held-out steps."""
+def evaluate(bie, net, scale, mus, G, test_idx, tol, rhs=None):
+    """GMRES iterations and solve times from each initial guess on the held-out steps. With rhs
+    (n -> (g_n, ms)), the right-hand side is recomputed per step and its time added to every method."""
     import torch
     res = {k: {"iters": [], "ms": []} for k in ("cold", "previous", "extrapolation", "network")}
     for n in test_idx:
-        g = G[n]
+        g, t_rhs = (G[n], 0.0) if rhs is None else rhs(n)
         guesses = {
             "cold": None,
             "previous": mus[n - 1],
@@ -102,7 +103,7 @@ def evaluate(bie, net, scale, mus, G, test_idx, tol):
             t0 = time.perf_counter()
             mu, it, rr = bie.solve(g, x0, tol)
             torch.cuda.synchronize()
-            dt = time.perf_counter() - t0 + (t_net if k == "network" else 0.0)
+            dt = time.perf_counter() - t0 + (t_net if k == "network" else 0.0) + t_rhs / 1000.0
             if not rr <= 10 * tol:
                 raise RuntimeError(f"GMRES from the {k} guess did not reach the tolerance ({rr:.2e})")
             res[k]["iters"].append(it)
@@ -141,3 +142,106 @@ def experiment(alpha, n_panels=256, n_train=2000, n_test=200, dt=1e-3, tol=1e-11
                 "held_out": ev}
     finally:
         bie.close()
+
+
+# --------------------------------------------------------------------------- coupled steps
+
+class StepProblem:
+    """Per-step right-hand side of the homogeneous problem (Sec. 2.2): the boundary velocity minus
+    the particular solution u^P = (d Psi/dy, -d Psi/dx), Psi the volume potential (modified-
+    biharmonic kernel) of the step's vorticity source, carried to the boundary nodes through the
+    leaf interpolants."""
+
+    def __init__(self, wl, bie, precision=VP_PREC_FP64):
+        import torch
+        self.wl, self.bie = wl, bie
+        self.vp = VolumePotential(I.KERNEL_MBIHARMONIC, wl.alpha, wl.p, wl.tree, precision=precision)
+        xy = self.vp.nodes()
+        self.X, self.Y = xy[0], xy[1]
+        self.bxy = bie.nodes[0:2].contiguous()
+        self.u = torch.empty(self.vp.N, dtype=torch.float64, device="cuda")
+        self.gradu = torch.empty(2, self.vp.N, dtype=torch.float64, device="cuda")
+
+    def rhs(self, t):
+        """g at time t (device [2N], interleaved per node) and the time of the volume part (ms)."""
+        import torch
+        f = self.wl.source(self.X, self.Y, t)
+        src, fs = self.wl.boundary(t)
+        ubc = bie_stokeslets(self.bie.alpha, torch.tensor(src, device="cuda"), torch.tensor(fs, device="cuda"),
+                             self.bxy)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        self.vp(f, self.u, self.gradu)
+        d = self.vp.interp(self.gradu, self.bxy)
+        g = (ubc - torch.stack([d[1], -d[0]])).t().contiguous().reshape(-1)
+        e1.record()
+        e1.synchronize()
+        return g, e0.elapsed_time(e1)
+
+    def close(self):
+        self.vp.close()
+
+
+def step_experiment(wl, n_panels=256, n_train=2000, n_test=200, tol=1e-11, precision=VP_PREC_FP64, epochs=40,
+                    batch=16, lr=1e-3, seed=5, width=64, n_layers=4, ksize=9, log=None):
+    """Steps of the coupled problem: plain solves for n_train + n_test + 3 steps, network training on
+    the first n_train, then per held-out step the volume potential, its boundary trace and GMRES from
+    each initial guess (step time = volume part + guess + GMRES)."""
+    import torch
+    bie = BIE(wl.alpha, R=1.0, A=0.3, k=5, phase=wl.phi, n_panels=n_panels, max_krylov=300)
+    prob = None
+    try:
+        prob = StepProblem(wl, bie, precision)
+        steps = n_train + n_test + 3
+        times = wl.dt * np.arange(steps)
+        t0 = time.perf_counter()
+        G, vp_ms = [], []
+        for k, t in enumerate(times):
+            g, ms = prob.rhs(float(t))
+            G.append(g); vp_ms.append(ms)
+            if log and k % 500 == 0:
+                log(f"rhs {k}/{steps}")
+        G = torch.stack(G)
+        t_rhs = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        mus, its = plain_solves(bie, G, tol)
+        t_plain = time.perf_counter() - t0
+        if log:
+            log(f"plain solves: mean {np.mean(its):.1f} iterations, {t_plain:.1f} s")
+        net = WarmStartNet(in_ch=8, width=width, out_ch=2, n_layers=n_layers, ksize=ksize, n=bie.N,
+                           max_batch=batch, seed=seed)
+        try:
+            t0 = time.perf_counter()
+            scale = train(net, mus, G, np.arange(3, 3 + n_train), epochs=epochs, batch=batch, lr=lr, seed=seed)
+            t_train = time.perf_counter() - t0
+            if log:
+                log(f"training: {t_train:.1f} s, loss {scale['losses'][0]:.3e} -> {np.mean(scale['losses'][-20:]):.3e}")
+            test_idx = np.arange(3 + n_train, steps)
+            ev = evaluate(bie, net, scale, mus, G, test_idx, tol, rhs=lambda n: prob.rhs(float(times[n])))
+        finally:
+            net.close()
+        return {"nodes": bie.N, "volume_nodes": prob.vp.N, "alpha": wl.alpha, "n_train": n_train, "n_test": n_test,
+                "tol": tol, "plain_mean_iters": float(np.mean(its)), "rhs_seconds": t_rhs,
+                "volume_ms_mean": float(np.mean(vp_ms[3:])), "plain_seconds": t_plain, "train_seconds": t_train,
+                "final_train_loss": float(np.mean(scale["losses"][-20:])), "first_train_loss": float(scale["losses"][0]),
+                "held_out": ev}
+    finally:
+        if prob is not None:
+            prob.close()
+        bie.close()
+
+
+def interior_error(bie, forcing, t, n_targets=64, seed=0, tol=1e-13):
+    """Accuracy of the discretisation: data from exterior stokeslets, whose field solves the
+    homogeneous problem inside; D[mu] against it at interior targets (radius <= 0.45)."""
+    import torch
+    src, f = forcing(t)
+    S, F = torch.tensor(src, device="cuda"), torch.tensor(f, device="cuda")
+    g = bie_stokeslets(bie.alpha, S, F, bie.nodes[0:2].contiguous()).t().contiguous().reshape(-1)
+    mu, it, rr = bie.solve(g, None, tol)
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(0, 0.45, n_targets); th = rng.uniform(0, 2 * np.pi, n_targets)
+    tx = torch.tensor(np.stack([r * np.cos(th), r * np.sin(th)]), device="cuda")
+    u = bie.eval(mu, tx)
+    ue = bie_stokeslets(bie.alpha, S, F, tx)
+    return float((u - ue).abs().max() / ue.abs().max()), it
