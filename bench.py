@@ -310,8 +310,23 @@ def run_steps(args):
     b = V.BIE(wl.alpha, R=1.0, A=0.3, k=5, phase=wl.phi, n_panels=256)
     try:
         err, _ = WS.interior_error(b, wl.boundary, 0.0)
+        # the Krylov operator apply (dense FP64 matrix-vector product, HBM-bound), timed with events
+        x = torch.randn(2 * b.N, dtype=torch.float64, device="cuda")
+        yv = torch.empty_like(x)
+        for _ in range(3):
+            b.apply(x, yv)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        for _ in range(20):
+            b.apply(x, yv)
+        e1.record(stream)
+        e1.synchronize()
+        gemv_ms = e0.elapsed_time(e1) / 20
+        gemv_bytes = (2 * b.N) ** 2 * 8 + 2 * (2 * b.N) * 8
     finally:
         b.close()
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
     ev = r["held_out"]
     line = {"metric": "coupled step time with the learned GMRES warm start", "value": ev["network"]["mean_ms"],
             "unit": "ms/step", "n_gpus": world, "steps": args.test_steps, "warmup": 3 + args.train_steps,
@@ -320,13 +335,16 @@ def run_steps(args):
             "config": {"workload": wl.name, "alpha": wl.alpha, "boundary_nodes": r["nodes"],
                        "volume_nodes": r["volume_nodes"], "volume_precision": args.precision,
                        "train_steps": args.train_steps, "test_steps": args.test_steps, "epochs": args.epochs,
-                       "gmres_tol": 1e-11, "net": "circular conv1d 8-64-64-64-2, kernel 9, fp32"},
+                       "gmres_tol": 1e-11, "net": "circular conv1d 10-64-64-64-2, kernel 9, fp32"},
             "held_out": ev,
             "iterations_saved_vs_cold": ev["cold"]["mean_iters"] - ev["network"]["mean_iters"],
             "iterations_saved_vs_extrapolation": ev["extrapolation"]["mean_iters"] - ev["network"]["mean_iters"],
             "plain_mean_iters": r["plain_mean_iters"], "volume_ms_mean": r["volume_ms_mean"],
             "train_seconds": r["train_seconds"], "train_loss": [r["first_train_loss"], r["final_train_loss"]],
             "interior_rel_err_exact_solution": err, "wall_seconds": wall,
+            "gmres_operator_roofline": {"kernel": "k_gemv (dense FP64 Nystrom matrix)", "bound": "hbm",
+                                        "achieved": gemv_bytes / (gemv_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                                        "frac": gemv_bytes / (gemv_ms / 1e3) / 1e9 / hbm, "ms": gemv_ms},
             "clocks": sampler.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)

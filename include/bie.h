@@ -40,16 +40,17 @@ int bie_size(bie b, int* n_nodes, double* boundary_length);
 /* Node data, device array [7][N]: x, y, n_x, n_y (inward unit normal), quadrature weight, curvature, t. */
 int bie_nodes(bie b, double* out, void* stream);
 
-/* out = (1/2 + D + W) mu (device arrays of 2N). */
+/* out = (1/2 + D + W) mu (device arrays of 2N; mu 16-byte aligned, else VP_ERR_ARG). */
 int bie_apply(bie b, const double* mu, double* out, void* stream);
 
 /*
  * bie_solve -- GMRES (no restart; classical Gram-Schmidt applied twice, FP64) for (1/2+D+W) mu = g.
  *  g      device [2N] right-hand side.
- *  mu     device [2N]: initial guess on entry (zeros for a cold start), solution on return.
+ *  mu     device [2N], 16-byte aligned: initial guess on entry (zeros for a cold start), solution on return.
  *  tol    stop when the residual estimate <= tol * |g|;  max_iter <= max_krylov of bie_create.
  *  iters  receives the number of iterations; relres the true relative residual |g - A mu| / |g|.
- * Synchronises `stream`.
+ * The Arnoldi steps run on the device; the host queues four iterations at a time and reads the
+ * device state between groups (steps queued past convergence do nothing). Synchronises `stream`.
  */
 int bie_solve(bie b, const double* g, double* mu, double tol, int max_iter, int* iters, double* relres, void* stream);
 

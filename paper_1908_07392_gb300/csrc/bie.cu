@@ -257,22 +257,49 @@ __global__ void __launch_bounds__(128) k_matrix_local(int np, double alpha, doub
 }
 
 // y = A x for a dense row-major n x n FP64 matrix: one warp per row.
-__global__ void k_gemv(int n, const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y) {
+// GMRES state on the device; every Krylov kernel returns at once when `done` is set, so the host
+// can queue several iterations ahead and look at the state only once per group.
+struct GmresCtl {
+  double bnorm, res, hn;
+  int done, it;
+};
+
+__device__ inline bool gm_done(const GmresCtl* c) { return c && *(volatile const int*)&c->done; }
+
+// y = A x, A row-major n x n (n even): one warp per row. The matrix is streamed once
+// (loads that bypass L1, four 16-byte loads in flight per lane); x stays in L1/L2.
+__global__ void k_gemv(int n, const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y,
+                       const GmresCtl* ctl = nullptr) {
+  if (gm_done(ctl)) return;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
-  const double* a = A + (size_t)row * n;
-  double s = 0.0;
-  for (int k = lane * 2; k < n; k += 64) {
-    const double2 av = *reinterpret_cast<const double2*>(a + k);
-    s += av.x * x[k] + av.y * x[k + 1];
+  const double2* a = reinterpret_cast<const double2*>(A + (size_t)row * n);
+  const double2* xv = reinterpret_cast<const double2*>(x);
+  const int n2 = n >> 1;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int k = lane;
+  for (; k + 96 < n2; k += 128) {
+    const double2 a0 = __ldcs(a + k), a1 = __ldcs(a + k + 32), a2 = __ldcs(a + k + 64), a3 = __ldcs(a + k + 96);
+    const double2 x0 = __ldg(xv + k), x1 = __ldg(xv + k + 32), x2 = __ldg(xv + k + 64), x3 = __ldg(xv + k + 96);
+    s0 = fma(a0.x, x0.x, fma(a0.y, x0.y, s0));
+    s1 = fma(a1.x, x1.x, fma(a1.y, x1.y, s1));
+    s2 = fma(a2.x, x2.x, fma(a2.y, x2.y, s2));
+    s3 = fma(a3.x, x3.x, fma(a3.y, x3.y, s3));
   }
+  for (; k < n2; k += 32) {
+    const double2 a0 = __ldcs(a + k), x0 = __ldg(xv + k);
+    s0 = fma(a0.x, x0.x, fma(a0.y, x0.y, s0));
+  }
+  double s = (s0 + s1) + (s2 + s3);
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) y[row] = s;
 }
 
 // h[c] = sum_k V[c][k] w[k] for c < ncols (V row-major [ncols][n]): one block per column.
-__global__ void k_dots(int n, int ncols, const double* __restrict__ V, const double* __restrict__ w, double* h) {
+__global__ void k_dots(int n, int ncols, const double* __restrict__ V, const double* __restrict__ w, double* h,
+                       const GmresCtl* ctl = nullptr) {
+  if (gm_done(ctl)) return;
   const int c = blockIdx.x;
   if (c >= ncols) return;
   __shared__ double red[32];
@@ -289,7 +316,9 @@ __global__ void k_dots(int n, int ncols, const double* __restrict__ V, const dou
 }
 
 // w -= sum_c h[c] V[c]
-__global__ void k_sub_proj(int n, int ncols, const double* __restrict__ V, const double* __restrict__ h, double* w) {
+__global__ void k_sub_proj(int n, int ncols, const double* __restrict__ V, const double* __restrict__ h, double* w,
+                           const GmresCtl* ctl = nullptr) {
+  if (gm_done(ctl)) return;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   double s = w[k];
@@ -302,13 +331,70 @@ __global__ void k_axpby(int n, double a, const double* x, double b, double* y) {
   if (k < n) y[k] = a * x[k] + b * y[k];
 }
 
-// x += sum_c coef[c] V[c]
-__global__ void k_add_comb(int n, int ncols, const double* __restrict__ V, const double* __restrict__ coef, double* x) {
+// x += sum_{c < it} y[c] V[c], it the iteration count in the GMRES state
+__global__ void k_add_comb(int n, const GmresCtl* ctl, const double* __restrict__ V, const double* __restrict__ coef,
+                           double* x) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
+  const int ncols = ctl->it;
   double s = x[k];
   for (int c = 0; c < ncols; ++c) s += coef[c] * V[(size_t)c * n + k];
   x[k] = s;
+}
+
+// Start of GMRES (one thread): norms from the dot products gr = (g.g, r.r).
+__global__ void k_gm_init(GmresCtl* ctl, const double* gr, double tol, double* gv) {
+  const double bnorm = gr[0] > 0.0 ? sqrt(gr[0]) : 1.0, beta = sqrt(fmax(gr[1], 0.0));
+  ctl->bnorm = bnorm;
+  ctl->res = beta / bnorm;
+  ctl->hn = beta;
+  ctl->it = 0;
+  ctl->done = (beta / bnorm <= tol || beta == 0.0) ? 1 : 0;
+  gv[0] = beta;
+}
+
+// y = x / ctl->hn (the next Krylov vector), skipped once converged.
+__global__ void k_gm_scale(int n, const GmresCtl* ctl, const double* __restrict__ x, double* __restrict__ y) {
+  if (gm_done(ctl)) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) y[k] = x[k] / ctl->hn;
+}
+
+// Arnoldi step j (one thread): Hessenberg column j from the two Gram-Schmidt passes hv0, hv1 and
+// |w|^2, earlier Givens rotations applied, new rotation, residual estimate |gv[j+1]| / |g|.
+__global__ void k_gm_step(int j, int m, double tol, GmresCtl* ctl, double* H, double* cs, double* sn, double* gv,
+                          const double* hv0, const double* hv1, const double* wn2) {
+  if (ctl->done) return;
+  for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv0[i] + hv1[i];
+  const double hn = sqrt(fmax(*wn2, 0.0));
+  H[(size_t)(j + 1) * m + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+    H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+    H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+  }
+  const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+  const double d = hypot(a, c);
+  cs[j] = d > 0.0 ? a / d : 1.0;
+  sn[j] = d > 0.0 ? c / d : 0.0;
+  H[(size_t)j * m + j] = d;
+  H[(size_t)(j + 1) * m + j] = 0.0;
+  gv[j + 1] = -sn[j] * gv[j];
+  gv[j] = cs[j] * gv[j];
+  ctl->it = j + 1;
+  ctl->hn = hn;
+  ctl->res = fabs(gv[j + 1]) / ctl->bnorm;
+  if (ctl->res <= tol || hn == 0.0) ctl->done = 1;
+}
+
+// Least-squares solution of the rotated Hessenberg system (one thread, back substitution).
+__global__ void k_gm_backsub(int m, const GmresCtl* ctl, const double* H, const double* gv, double* y) {
+  const int it = ctl->it;
+  for (int i = it - 1; i >= 0; --i) {
+    double t = gv[i];
+    for (int k = i + 1; k < it; ++k) t -= H[(size_t)i * m + k] * y[k];
+    y[i] = t / H[(size_t)i * m + i];
+  }
 }
 
 // u(x_t) = sum_j D(x_t, y_j) mu_j w_j (targets away from the boundary).
@@ -376,7 +462,10 @@ struct bie_s {
   double* A = nullptr;
   // GMRES work space
   int m = 0;
-  double *V = nullptr, *w = nullptr, *h = nullptr, *r = nullptr;
+  double *V = nullptr, *w = nullptr, *r = nullptr;
+  double* gm = nullptr;          // H [(m+1) m], cs [m], sn [m], gv [m+2], y [m], hv [2(m+1)], scalars [8]
+  vp::GmresCtl* ctl = nullptr;   // device
+  vp::GmresCtl* hctl = nullptr;  // pinned host copy
 };
 
 using namespace vp;
@@ -394,6 +483,7 @@ int dalloc(bie_s* b, T** p, size_t n) {
 
 extern "C" void bie_free(bie b) {
   if (!b) return;
+  if (b->hctl) cudaFreeHost(b->hctl);
   for (void* p : b->allocs) cudaFree(p);
   delete b;
 }
@@ -433,9 +523,16 @@ extern "C" int bie_create(double alpha, double R, double A, int k, double phase,
     if ((rc = dalloc(B.get(), p, N))) { bie_free(B.release()); return rc; }
   if ((rc = dalloc(B.get(), &B->A, (size_t)B->n2 * B->n2))) { bie_free(B.release()); return rc; }
   if ((rc = dalloc(B.get(), &B->V, (size_t)(B->m + 1) * B->n2)) || (rc = dalloc(B.get(), &B->w, B->n2)) ||
-      (rc = dalloc(B.get(), &B->h, 2 * (B->m + 1))) || (rc = dalloc(B.get(), &B->r, B->n2))) {
+      (rc = dalloc(B.get(), &B->r, B->n2)) ||
+      (rc = dalloc(B.get(), &B->gm, (size_t)(B->m + 1) * B->m + 6 * (size_t)B->m + 12)) ||
+      (rc = dalloc(B.get(), &B->ctl, 1))) {
     bie_free(B.release());
     return rc;
+  }
+  if (cudaHostAlloc(&B->hctl, sizeof(GmresCtl), cudaHostAllocDefault) != cudaSuccess) {
+    B->hctl = nullptr;
+    bie_free(B.release());
+    return VP_ERR_OOM;
   }
   k_nodes<<<(N + 127) / 128, 128, 0, s>>>(B->star, B->np, nd);
   // boundary length
@@ -477,7 +574,7 @@ extern "C" int bie_nodes(bie b, double* out, void* stream) {
 }
 
 extern "C" int bie_apply(bie b, const double* mu, double* out, void* stream) {
-  if (!b || !mu || !out) return VP_ERR_ARG;
+  if (!b || !mu || !out || (reinterpret_cast<uintptr_t>(mu) & 15)) return VP_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_gemv<<<(b->n2 * 32 + 255) / 256, 256, 0, s>>>(b->n2, b->A, mu, out);
   TRY(cudaGetLastError());
@@ -486,86 +583,58 @@ extern "C" int bie_apply(bie b, const double* mu, double* out, void* stream) {
 
 extern "C" int bie_solve(bie b, const double* g, double* mu, double tol, int max_iter, int* iters, double* relres,
                          void* stream) {
-  if (!b || !g || !mu || !(tol > 0.0) || max_iter < 1) return VP_ERR_ARG;
+  if (!b || !g || !mu || !(tol > 0.0) || max_iter < 1 || (reinterpret_cast<uintptr_t>(mu) & 15)) return VP_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int n = b->n2;
-  const int m = std::min(max_iter, b->m);
-  const int T = 256, G = (n + T - 1) / T;
-  // r = g - A mu
-  k_gemv<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, b->A, mu, b->r);
+  const int n = b->n2, M = b->m;
+  const int m = std::min(max_iter, M);
+  const int T = 256, G = (n + T - 1) / T, GV = (n * 32 + 255) / 256;
+  double* H = b->gm;
+  double* cs = H + (size_t)(M + 1) * M;
+  double* sn = cs + M;
+  double* gv = sn + M;
+  double* y = gv + M + 2;
+  double* hv = y + M;
+  double* wn2 = hv + 2 * (M + 1);
+  GmresCtl* ctl = b->ctl;
+  // r = g - A mu, norms, V0 = r / |r|
+  k_gemv<<<GV, 256, 0, s>>>(n, b->A, mu, b->r);
   k_axpby<<<G, T, 0, s>>>(n, 1.0, g, -1.0, b->r);
-  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), gv(m + 2, 0.0), hv(2 * (m + 1));
-  double bnorm = 0.0, beta = 0.0;
-  k_dots<<<1, 256, 0, s>>>(n, 1, g, g, b->h);
-  k_dots<<<1, 256, 0, s>>>(n, 1, b->r, b->r, b->h + 1);
-  TRY(cudaMemcpyAsync(hv.data(), b->h, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  TRY(cudaStreamSynchronize(s));
-  bnorm = std::sqrt(hv[0]);
-  beta = std::sqrt(hv[1]);
-  if (bnorm == 0.0) bnorm = 1.0;
-  int it = 0;
-  double res = beta / bnorm;
-  if (res > tol) {
-    // V0 = r / beta
-    TRY(cudaMemsetAsync(b->V, 0, (size_t)n * sizeof(double), s));
-    k_axpby<<<G, T, 0, s>>>(n, 1.0 / beta, b->r, 0.0, b->V);
-    gv[0] = beta;
-    for (int j = 0; j < m; ++j) {
-      double* vj = b->V + (size_t)j * n;
-      double* vn = b->V + (size_t)(j + 1) * n;
-      k_gemv<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, b->A, vj, b->w);
-      // classical Gram-Schmidt, twice
+  k_dots<<<1, 256, 0, s>>>(n, 1, g, g, wn2);
+  k_dots<<<1, 256, 0, s>>>(n, 1, b->r, b->r, wn2 + 1);
+  k_gm_init<<<1, 1, 0, s>>>(ctl, wn2, tol, gv);
+  k_gm_scale<<<G, T, 0, s>>>(n, ctl, b->r, b->V);
+  // Arnoldi with classical Gram-Schmidt applied twice; the host queues kGroup iterations at a time
+  // and reads the device state after each group (iterations past convergence are no-ops).
+  constexpr int kGroup = 4;
+  for (int j = 0; j < m;) {
+    const int jend = std::min(m, j + kGroup);
+    for (; j < jend; ++j) {
+      const double* vj = b->V + (size_t)j * n;
+      k_gemv<<<GV, 256, 0, s>>>(n, b->A, vj, b->w, ctl);
       for (int pass = 0; pass < 2; ++pass) {
-        k_dots<<<j + 1, 256, 0, s>>>(n, j + 1, b->V, b->w, b->h + pass * (m + 1));
-        k_sub_proj<<<G, T, 0, s>>>(n, j + 1, b->V, b->h + pass * (m + 1), b->w);
+        k_dots<<<j + 1, 256, 0, s>>>(n, j + 1, b->V, b->w, hv + pass * (M + 1), ctl);
+        k_sub_proj<<<G, T, 0, s>>>(n, j + 1, b->V, hv + pass * (M + 1), b->w, ctl);
       }
-      k_dots<<<1, 256, 0, s>>>(n, 1, b->w, b->w, b->r);
-      TRY(cudaMemcpyAsync(hv.data(), b->h, 2 * (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-      double wn2 = 0.0;
-      TRY(cudaMemcpyAsync(&wn2, b->r, sizeof(double), cudaMemcpyDeviceToHost, s));
-      TRY(cudaStreamSynchronize(s));
-      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hv[i] + hv[m + 1 + i];
-      const double hn = std::sqrt(std::max(wn2, 0.0));
-      H[(size_t)(j + 1) * m + j] = hn;
-      if (hn > 0.0) k_axpby<<<G, T, 0, s>>>(n, 1.0 / hn, b->w, 0.0, vn);
-      // Givens rotations
-      for (int i = 0; i < j; ++i) {
-        const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
-        H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
-      }
-      const double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-      const double d = std::hypot(a, c);
-      cs[j] = d > 0.0 ? a / d : 1.0;
-      sn[j] = d > 0.0 ? c / d : 0.0;
-      H[(size_t)j * m + j] = d;
-      H[(size_t)(j + 1) * m + j] = 0.0;
-      gv[j + 1] = -sn[j] * gv[j];
-      gv[j] = cs[j] * gv[j];
-      it = j + 1;
-      res = std::fabs(gv[j + 1]) / bnorm;
-      if (res <= tol || hn == 0.0) break;
+      k_dots<<<1, 256, 0, s>>>(n, 1, b->w, b->w, wn2 + 2, ctl);
+      k_gm_step<<<1, 1, 0, s>>>(j, M, tol, ctl, H, cs, sn, gv, hv, hv + M + 1, wn2 + 2);
+      k_gm_scale<<<G, T, 0, s>>>(n, ctl, b->w, b->V + (size_t)(j + 1) * n);
     }
-    // back substitution and update
-    std::vector<double> y(it, 0.0);
-    for (int i = it - 1; i >= 0; --i) {
-      double t = gv[i];
-      for (int k2 = i + 1; k2 < it; ++k2) t -= H[(size_t)i * m + k2] * y[k2];
-      y[i] = t / H[(size_t)i * m + i];
-    }
-    TRY(cudaMemcpyAsync(b->h, y.data(), it * sizeof(double), cudaMemcpyHostToDevice, s));
-    k_add_comb<<<G, T, 0, s>>>(n, it, b->V, b->h, mu);
-    // true residual
-    k_gemv<<<(n * 32 + 255) / 256, 256, 0, s>>>(n, b->A, mu, b->r);
-    k_axpby<<<G, T, 0, s>>>(n, 1.0, g, -1.0, b->r);
-    k_dots<<<1, 256, 0, s>>>(n, 1, b->r, b->r, b->h);
-    double rr = 0.0;
-    TRY(cudaMemcpyAsync(&rr, b->h, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRY(cudaMemcpyAsync(b->hctl, ctl, sizeof(GmresCtl), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
-    res = std::sqrt(rr) / bnorm;
+    if (b->hctl->done) break;
   }
-  if (iters) *iters = it;
-  if (relres) *relres = res;
+  // update and the true residual
+  k_gm_backsub<<<1, 1, 0, s>>>(M, ctl, H, gv, y);
+  k_add_comb<<<G, T, 0, s>>>(n, ctl, b->V, y, mu);
+  k_gemv<<<GV, 256, 0, s>>>(n, b->A, mu, b->r);
+  k_axpby<<<G, T, 0, s>>>(n, 1.0, g, -1.0, b->r);
+  k_dots<<<1, 256, 0, s>>>(n, 1, b->r, b->r, wn2 + 3);
+  double rr[2] = {0.0, 0.0};
+  TRY(cudaMemcpyAsync(b->hctl, ctl, sizeof(GmresCtl), cudaMemcpyDeviceToHost, s));
+  TRY(cudaMemcpyAsync(rr, wn2 + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  if (iters) *iters = b->hctl->it;
+  if (relres) *relres = std::sqrt(std::max(rr[0], 0.0)) / b->hctl->bnorm;
   TRY(cudaGetLastError());
   return VP_OK;
 }

@@ -1,9 +1,10 @@
 """Learned warm start for the per-step boundary integral equation.
 
 A sequence of steps n = 0, 1, ... each solves (1/2 + D + W) mu_n = g_n by GMRES (library). The
-network (library kernels) sees the last three densities and the current boundary data, all scaled
-by fixed factors, and predicts the correction to the cubic extrapolation 3 mu_{n-1} - 3 mu_{n-2}
-+ mu_{n-3}; its output, scaled back and added to that extrapolation, is the initial guess. It is
+network (library kernels) sees the last three densities, the current boundary data and the residual
+of the cubic extrapolation 3 mu_{n-1} - 3 mu_{n-2} + mu_{n-3} (one operator apply), all scaled by
+fixed factors, and predicts the correction to that extrapolation; its output, scaled back and added
+to the extrapolation, is the initial guess. It is
 trained on densities that plain (cold-start) GMRES solves produce. Plain GMRES to the same residual
 stays the solver and the judge of the result: the guess only changes where GMRES starts.
 """
@@ -40,45 +41,72 @@ def plain_solves(bie, G, tol):
     return torch.stack(mus), its
 
 
-def _features(mus, G, n, s_mu, s_g):
-    """Network inputs [B][8][N] and the cubic extrapolation [B][2N] for steps n (index array)."""
+def _extrapolation(mus, n):
+    return 3 * mus[n - 1] - 3 * mus[n - 2] + mus[n - 3]
+
+
+def residuals(bie, mus, G, idx):
+    """r_n = g_n - A (3 mu_{n-1} - 3 mu_{n-2} + mu_{n-3}) for the steps idx ([len(idx)][2N])."""
+    import torch
+    return torch.stack([G[n] - bie.apply(_extrapolation(mus, n)) for n in idx])
+
+
+def _features(mus, G, R, n, scale):
+    """Network inputs [B][10][N] for steps n (index tensor), formed in FP64 and then rounded to FP32:
+    the last density, its first and second backward differences, the boundary data and the residual
+    R of the cubic extrapolation (rows matching n), each over its own fixed scale (differences are
+    scaled separately so that FP32 keeps them); and the extrapolation itself [B][2N]."""
     import torch
     N = mus.shape[1] // 2
-    ch = []
-    for lag in (1, 2, 3):
-        ch.append(mus[n - lag].reshape(-1, N, 2).permute(0, 2, 1) / s_mu)
-    ch.append(G[n].reshape(-1, N, 2).permute(0, 2, 1) / s_g)
+    m1, m2, m3 = mus[n - 1], mus[n - 2], mus[n - 3]
+    parts = [(m1, "s_mu"), (m1 - m2, "s_d1"), (m1 - 2 * m2 + m3, "s_d2"), (G[n], "s_g"), (R, "s_r")]
+    ch = [(v / scale[k]).reshape(-1, N, 2).permute(0, 2, 1) for v, k in parts]
     x = torch.cat(ch, dim=1).float().contiguous()
-    ext = 3 * mus[n - 1] - 3 * mus[n - 2] + mus[n - 3]
-    return x, ext
+    return x, _extrapolation(mus, n)
 
 
-def train(net, mus, G, train_idx, epochs=40, batch=16, lr=1e-3, seed=0):
+IN_CHANNELS = 10
+
+
+def train(bie, net, mus, G, train_idx, epochs=40, batch=16, lr=1e-3, seed=0):
     import torch
-    s_mu = float(mus.std()) or 1.0
-    s_g = float(G.std()) or 1.0
     N = mus.shape[1] // 2
-    err = mus[train_idx] - (3 * mus[train_idx - 1] - 3 * mus[train_idx - 2] + mus[train_idx - 3])
-    s_err = float(err.std()) or 1.0
+    R = torch.zeros_like(mus)
+    R[train_idx] = residuals(bie, mus, G, train_idx)
+    err = mus[train_idx] - _extrapolation(mus, train_idx)
+    d1 = mus[train_idx - 1] - mus[train_idx - 2]
+    d2 = mus[train_idx - 1] - 2 * mus[train_idx - 2] + mus[train_idx - 3]
+    scale = {k: (float(v.std()) or 1.0) for k, v in
+             (("s_mu", mus[train_idx]), ("s_d1", d1), ("s_d2", d2), ("s_g", G[train_idx]), ("s_r", R[train_idx]),
+              ("s_err", err))}
     rng = np.random.default_rng(seed)
     losses = []
     for ep in range(epochs):
         order = rng.permutation(train_idx)
         for k in range(0, len(order) - batch + 1, batch):
             n = torch.tensor(order[k:k + batch], device="cuda")
-            x, ext = _features(mus, G, n, s_mu, s_g)
-            t = ((mus[n] - ext).reshape(-1, N, 2).permute(0, 2, 1) / s_err).float().contiguous()
+            x, ext = _features(mus, G, R[n], n, scale)
+            t = ((mus[n] - ext).reshape(-1, N, 2).permute(0, 2, 1) / scale["s_err"]).float().contiguous()
             losses.append(net.train_step(x, t, lr))
-    return {"s_mu": s_mu, "s_g": s_g, "s_err": s_err, "losses": losses}
+    return dict(scale, losses=losses)
 
 
-def guess(net, scale, mus, G, n):
+def guess(bie, net, scale, mus, G, n):
+    """Network guess for step n, kept only if its residual is below that of the extrapolation
+    (one extra operator apply); returns (guess, whether the network's guess was kept, the ratio of
+    the two residual norms)."""
     import torch
     N = mus.shape[1] // 2
     idx = torch.tensor([n], device="cuda")
-    x, ext = _features(mus, G, idx, scale["s_mu"], scale["s_g"])
+    r = residuals(bie, mus, G, [n])
+    x, ext = _features(mus, G, r, idx, scale)
     y = net.forward(x)[0]                                   # [2][N]
-    return ext[0] + scale["s_err"] * y.permute(1, 0).reshape(-1).double()
+    cand = ext[0] + scale["s_err"] * y.permute(1, 0).reshape(-1).double()
+    rc = G[n] - bie.apply(cand)
+    ratio = float(rc.norm()) / max(float(r[0].norm()), 1e-300)
+    if ratio < 1.0:
+        return cand, True, ratio
+    return ext[0], False, ratio
 
 
 def evaluate(bie, net, scale, mus, G, test_idx, tol, rhs=None):
@@ -86,16 +114,19 @@ def evaluate(bie, net, scale, mus, G, test_idx, tol, rhs=None):
     (n -> (g_n, ms)), the right-hand side is recomputed per step and its time added to every method."""
     import torch
     res = {k: {"iters": [], "ms": []} for k in ("cold", "previous", "extrapolation", "network")}
+    kept, ratios = 0, []
     for n in test_idx:
         g, t_rhs = (G[n], 0.0) if rhs is None else rhs(n)
         guesses = {
             "cold": None,
             "previous": mus[n - 1],
-            "extrapolation": 3 * mus[n - 1] - 3 * mus[n - 2] + mus[n - 3],
+            "extrapolation": _extrapolation(mus, n),
         }
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        guesses["network"] = guess(net, scale, mus, G, n)
+        guesses["network"], used, ratio = guess(bie, net, scale, mus, G, n)
+        kept += int(used)
+        ratios.append(ratio)
         torch.cuda.synchronize()
         t_net = time.perf_counter() - t0
         for k, x0 in guesses.items():
@@ -108,8 +139,11 @@ def evaluate(bie, net, scale, mus, G, test_idx, tol, rhs=None):
                 raise RuntimeError(f"GMRES from the {k} guess did not reach the tolerance ({rr:.2e})")
             res[k]["iters"].append(it)
             res[k]["ms"].append(1000 * dt)
-    return {k: {"mean_iters": float(np.mean(v["iters"])), "max_iters": int(np.max(v["iters"])),
-                "mean_ms": float(np.mean(v["ms"]))} for k, v in res.items()}
+    out = {k: {"mean_iters": float(np.mean(v["iters"])), "max_iters": int(np.max(v["iters"])),
+               "mean_ms": float(np.mean(v["ms"]))} for k, v in res.items()}
+    out["network"]["kept_fraction"] = kept / max(1, len(test_idx))
+    out["network"]["residual_ratio_vs_extrapolation"] = float(np.exp(np.mean(np.log(ratios))))
+    return out
 
 
 def experiment(alpha, n_panels=256, n_train=2000, n_test=200, dt=1e-3, tol=1e-11, epochs=40, batch=16,
@@ -126,11 +160,11 @@ def experiment(alpha, n_panels=256, n_train=2000, n_test=200, dt=1e-3, tol=1e-11
         G = boundary_data(bie, forcing, times)
         mus, its = plain_solves(bie, G, tol)
         t_plain = time.perf_counter() - t0
-        net = WarmStartNet(in_ch=8, width=width, out_ch=2, n_layers=n_layers, ksize=ksize, n=bie.N,
+        net = WarmStartNet(in_ch=IN_CHANNELS, width=width, out_ch=2, n_layers=n_layers, ksize=ksize, n=bie.N,
                            max_batch=batch, seed=seed)
         try:
             t0 = time.perf_counter()
-            scale = train(net, mus, G, np.arange(3, 3 + n_train), epochs=epochs, batch=batch, lr=lr, seed=seed)
+            scale = train(bie, net, mus, G, np.arange(3, 3 + n_train), epochs=epochs, batch=batch, lr=lr, seed=seed)
             t_train = time.perf_counter() - t0
             test_idx = np.arange(3 + n_train, steps)
             ev = evaluate(bie, net, scale, mus, G, test_idx, tol)
@@ -208,11 +242,11 @@ def step_experiment(wl, n_panels=256, n_train=2000, n_test=200, tol=1e-11, preci
         t_plain = time.perf_counter() - t0
         if log:
             log(f"plain solves: mean {np.mean(its):.1f} iterations, {t_plain:.1f} s")
-        net = WarmStartNet(in_ch=8, width=width, out_ch=2, n_layers=n_layers, ksize=ksize, n=bie.N,
+        net = WarmStartNet(in_ch=IN_CHANNELS, width=width, out_ch=2, n_layers=n_layers, ksize=ksize, n=bie.N,
                            max_batch=batch, seed=seed)
         try:
             t0 = time.perf_counter()
-            scale = train(net, mus, G, np.arange(3, 3 + n_train), epochs=epochs, batch=batch, lr=lr, seed=seed)
+            scale = train(bie, net, mus, G, np.arange(3, 3 + n_train), epochs=epochs, batch=batch, lr=lr, seed=seed)
             t_train = time.perf_counter() - t0
             if log:
                 log(f"training: {t_train:.1f} s, loss {scale['losses'][0]:.3e} -> {np.mean(scale['losses'][-20:]):.3e}")
