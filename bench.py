@@ -7,14 +7,22 @@ the leaf Legendre tail is below 1e-11 (max depth 10) for a seeded star-shaped
 source with a C-infinity blend of width 0.05 plus 20 narrow Gaussians.
 
 A step is one vp_eval (every stage of the volume potential) over the resident
-source. L2 is flushed (a 512 MB write) before every timed step. The dominant
-kernel (the near-field table contraction) is timed live with CUDA events on
-the launching stream (vp_eval_timed). The e2e figure runs vp_eval_host from
-pinned host buffers (host-to-device copy of f and device-to-host copy of u and
-grad u inside the timed region). The CPU baseline is the FP64 oracle on a
-bounded sample of targets of the same workload.
+source. L2 is flushed (a 512 MB write) before every timed step. By default the
+headline value is the split-precision form (sliced bf16 tensor-core
+contractions, 1e-9 against the FP64 oracle) and the plain FP64 form (1e-10) is
+measured beside it in the same run ("plain_fp64", "split_speedup_vs_fp64").
+The dominant kernel (the near-field table contraction) is timed live with CUDA
+events on the launching stream (vp_eval_timed). The e2e figure runs
+vp_eval_host from pinned host buffers (host-to-device copy of f and
+device-to-host copy of u and grad u inside the timed region). The CPU baseline
+is the FP64 oracle on a bounded sample of targets of the same workload.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--alpha A] [--precision fp64|split]
+Other workloads: --workload batched (64 trees in one CUDA graph) and
+--workload steps (coupled volume potential + boundary integral equation steps
+with the learned GMRES warm start).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                       [--precision both|fp64|split] [--workload star|batched|steps]
 """
 from __future__ import annotations
 
@@ -43,7 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--alpha", type=float, default=300.0)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "split"],
+                    help="both (default): split-precision headline plus the plain FP64 form beside it")
     ap.add_argument("--order", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -195,8 +204,6 @@ def run_reference(args):
 
 def choose_engine(V, args, tree, f, u, g):
     """Engine of the split-precision contractions; returns the number of launches on tcgen05."""
-    if args.precision != "split":
-        return 0
     if args.engine == "mma":
         V.vp_tree_set_engine(tree, V.ENGINE_MMA_SYNC)
         return 0
@@ -204,6 +211,67 @@ def choose_engine(V, args, tree, f, u, g):
         V.vp_tree_set_engine(tree, V.ENGINE_TCGEN05)
         return -1
     return V.vp_autotune(tree, f, u, g)
+
+
+def batched_form(args, V, ws, prec, local):
+    """One form (FP64 or split) of the batched workload: graph replay timed per step, L2 flushed."""
+    import torch
+    t0 = time.perf_counter()
+    vps = [V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, order=args.order, precision=prec) for w in ws]
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    batch = None
+    try:
+        fs = [torch.from_numpy(w.f).cuda() for w in ws]
+        us = [torch.empty_like(f) for f in fs]
+        gs = [torch.empty(2, f.numel(), dtype=torch.float64, device="cuda") for f in fs]
+        trees = [vp.tree for vp in vps]
+        n_tc = sum(choose_engine(V, args, vp.tree, f, u, g) for vp, f, u, g in zip(vps, fs, us, gs)) \
+            if prec == V.VP_PREC_SPLIT else 0
+        batch = V.vp_batch_create(trees, fs, us, gs, n_streams=args.streams)
+        nodes, launches = V.vp_batch_stats(batch)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        stream = torch.cuda.current_stream()
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            total = 0.0
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream); fn(); e1.record(stream); e1.synchronize()
+                total += e0.elapsed_time(e1)
+            return total
+
+        sampler = ClockSampler(local)
+        with sampler:
+            graph_ms = timed(lambda: V.vp_batch_run(batch))
+        serial_ms = timed(lambda: V.vp_eval_batched(trees, fs, us, gs, use_graph=0))
+        # dominant kernel: the near-field contraction of the largest tree, timed with events
+        big = max(range(len(ws)), key=lambda k: ws[k].n_nodes)
+        ms = [V.vp_eval_timed(vps[big].tree, fs[big], us[big], gs[big]) for _ in range(3)]
+        _, sf = V.vp_tree_stats(vps[big].tree)
+        near_ms = statistics.mean(m[4] for m in ms)
+        if prec == V.VP_PREC_FP64:
+            achieved = sf[4] / (near_ms / 1e3) / 1e12
+            peak = N_SM * 2070.0e6 * FP64_FLOPS_PER_CLK_PER_SM / 1e12
+            roof = {"kernel": "k_gemm_gather_f64<1> (near tables, largest tree)", "bound": "alu"}
+        else:
+            achieved = sf[4] * 21 / (near_ms / 1e3) / 1e12
+            peak = measured_peaks().get("bf16_tflops", 1900.0)
+            roof = {"kernel": "split-precision near GEMM, engine per launch (largest tree)", "bound": "tensor",
+                    "peak_source": "measured dense bf16 burst, of measured"}
+        return {"nodes": int(nodes), "launches": int(launches), "graph_ms": graph_ms, "serial_ms": serial_ms,
+                "setup_s": setup_s, "n_tc": n_tc, "clocks": sampler.summary(),
+                "roofline": dict(roof, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                                 traffic=None)}
+    finally:
+        if batch is not None:
+            V.vp_batch_free(batch)
+        for vp in vps:
+            vp.close()
 
 
 def run_batched(args):
@@ -215,73 +283,33 @@ def run_batched(args):
     torch.cuda.set_device(local)
     B.build()
     ws = I.batched_workloads(seed=4 + rank)
-    prec = V.VP_PREC_SPLIT if args.precision == "split" else V.VP_PREC_FP64
-    t0 = time.perf_counter()
-    vps = [V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, order=args.order, precision=prec) for w in ws]
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
-    fs = [torch.from_numpy(w.f).cuda() for w in ws]
-    us = [torch.empty_like(f) for f in fs]
-    gs = [torch.empty(2, f.numel(), dtype=torch.float64, device="cuda") for f in fs]
-    trees = [vp.tree for vp in vps]
-    n_tc = sum(choose_engine(V, args, vp.tree, f, u, g) for vp, f, u, g in zip(vps, fs, us, gs))
-    batch = V.vp_batch_create(trees, fs, us, gs, n_streams=args.streams)
-    nodes, launches = V.vp_batch_stats(batch)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        total = 0.0
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream); fn(); e1.record(stream); e1.synchronize()
-            total += e0.elapsed_time(e1)
-        return total
-
-    sampler = ClockSampler(local)
-    with sampler:
-        graph_ms = timed(lambda: V.vp_batch_run(batch))
-    serial_ms = timed(lambda: V.vp_eval_batched(trees, fs, us, gs, use_graph=0))
-    value = nodes * args.steps / (graph_ms / 1000.0)
-    # dominant kernel: the near-field contraction of the largest tree, timed with events
-    big = max(range(len(ws)), key=lambda k: ws[k].n_nodes)
-    ms = [V.vp_eval_timed(vps[big].tree, fs[big], us[big], gs[big]) for _ in range(3)]
-    _, sf = V.vp_tree_stats(vps[big].tree)
-    near_ms = statistics.mean(m[4] for m in ms)
-    if prec == V.VP_PREC_FP64:
-        achieved = sf[4] / (near_ms / 1e3) / 1e12
-        peak = N_SM * 2070.0e6 * FP64_FLOPS_PER_CLK_PER_SM / 1e12
-        roof = {"kernel": "k_gemm_gather_f64<1> (near tables, largest tree)", "bound": "alu"}
-    else:
-        achieved = sf[4] * 21 / (near_ms / 1e3) / 1e12
-        peak = measured_peaks().get("bf16_tflops", 1900.0)
-        roof = {"kernel": "k_split_gemm<6> (near tables, largest tree)", "bound": "tensor"}
-    V.vp_batch_free(batch)
-    import numpy as np
+    head_prec = V.VP_PREC_FP64 if args.precision == "fp64" else V.VP_PREC_SPLIT
+    head = batched_form(args, V, ws, head_prec, local)
+    plain = batched_form(args, V, ws, V.VP_PREC_FP64, local) if args.precision == "both" else None
+    split = head_prec == V.VP_PREC_SPLIT
     line = {"metric": "volume-potential leaf-nodes/s at stated rel err, split/batched vs plain FP64",
-            "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": graph_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == V.VP_PREC_FP64 else "f64+f16-slices",
-            "data": "synthetic",
+            "value": head["nodes"] * args.steps / (head["graph_ms"] / 1000.0), "unit": "nodes/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["graph_ms"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+bf16-slices" if split else "f64", "data": "synthetic",
             "config": {"workload": "batched: 64 trees, nodes log-uniform [1e4, 5e5], alpha log-uniform [10, 1000], "
                                    "p in {8, 12, 16}, modified-Helmholtz kernel, Gaussian-sum sources",
-                       "trees": len(ws), "nodes": int(nodes), "max_depth": int(max(w.tree.max_level for w in ws)),
-                       "precision": args.precision, "streams": args.streams, "setup_s": round(setup_s, 1),
-                       "engine": args.engine if prec == V.VP_PREC_SPLIT else "fp64", "tcgen05_launches": n_tc,
+                       "trees": len(ws), "nodes": head["nodes"], "max_depth": int(max(w.tree.max_level for w in ws)),
+                       "precision": "split" if split else "fp64", "stated_rel_err": 1e-9 if split else 1e-10,
+                       "streams": args.streams, "setup_s": round(head["setup_s"], 1),
+                       "engine": args.engine if split else "fp64", "tcgen05_launches": head["n_tc"],
                        "l2": "flushed before every timed step (512 MB write)"},
-            "serial_ms_per_step": serial_ms / args.steps,
-            "graph_speedup_vs_serial": serial_ms / graph_ms,
-            "roofline": dict(roof, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak, traffic=None),
-            "cpu_baseline": None, "e2e": None, "gpu_launches": int(launches) * args.steps,
-            "clocks": sampler.summary()}
+            "serial_ms_per_step": head["serial_ms"] / args.steps,
+            "graph_speedup_vs_serial": head["serial_ms"] / head["graph_ms"],
+            "roofline": head["roofline"], "cpu_baseline": None, "e2e": None,
+            "gpu_launches": head["launches"] * args.steps, "clocks": head["clocks"]}
+    if plain is not None:
+        pv = plain["nodes"] * args.steps / (plain["graph_ms"] / 1000.0)
+        line["plain_fp64"] = {"value": pv, "unit": "nodes/s", "ms_per_step": plain["graph_ms"] / args.steps,
+                              "roofline": plain["roofline"]}
+        line["split_speedup_vs_fp64"] = line["value"] / pv
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for vp in vps:
-        vp.close()
 
 
 def run_steps(args):
@@ -299,7 +327,7 @@ def run_steps(args):
     torch.cuda.set_device(local)
     B.build()
     wl = I.step_workload(seed=5 + rank)
-    prec = V.VP_PREC_SPLIT if args.precision == "split" else V.VP_PREC_FP64
+    prec = V.VP_PREC_FP64 if args.precision == "fp64" else V.VP_PREC_SPLIT
     log = (lambda m: print(m, file=sys.stderr, flush=True)) if rank == 0 else None
     t0 = time.perf_counter()
     sampler = ClockSampler(local)
@@ -333,7 +361,7 @@ def run_steps(args):
             "ms_per_step": ev["network"]["mean_ms"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 solve, f32 network", "data": "synthetic",
             "config": {"workload": wl.name, "alpha": wl.alpha, "boundary_nodes": r["nodes"],
-                       "volume_nodes": r["volume_nodes"], "volume_precision": args.precision,
+                       "volume_nodes": r["volume_nodes"], "volume_precision": "fp64" if prec == V.VP_PREC_FP64 else "split",
                        "train_steps": args.train_steps, "test_steps": args.test_steps, "epochs": args.epochs,
                        "gmres_tol": 1e-11, "net": "circular conv1d 10-64-64-64-2, kernel 9, fp32"},
             "held_out": ev,
@@ -348,6 +376,98 @@ def run_steps(args):
             "clocks": sampler.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measure(args, V, w, prec, world, local, with_e2e):
+    """Time args.steps evaluations of one form (FP64 or split) of the workload; per-step L2 flush."""
+    import torch
+    t0 = time.perf_counter()
+    vp = V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, order=args.order, precision=prec)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    try:
+        N = vp.N
+        f = torch.from_numpy(w.f).cuda()
+        u = torch.empty(N, dtype=torch.float64, device="cuda")
+        g = torch.empty(2, N, dtype=torch.float64, device="cuda")
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        launches, stage_flops = V.vp_tree_stats(vp.tree)
+        stream = torch.cuda.current_stream()
+        n_tc = choose_engine(V, args, vp.tree, f, u, g) if prec == V.VP_PREC_SPLIT else 0
+        for _ in range(args.warmup):
+            V.vp_eval(vp.tree, f, u, g)
+        torch.cuda.synchronize()
+
+        def barrier():
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            torch.cuda.synchronize()
+
+        stage_ms, step_ms = [], []
+        sampler = ClockSampler(local)
+        barrier()
+        with sampler:
+            for _ in range(args.steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ms = V.vp_eval_timed(vp.tree, f, u, g)
+                e1.record(stream)
+                e1.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+                stage_ms.append(ms)
+        barrier()
+        total_ms = sum(step_ms)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        value = world * N * args.steps / (total_ms / 1000.0)
+
+        # e2e: host buffers, copies inside the timed region
+        e2e = None
+        if with_e2e:
+            fh = torch.from_numpy(w.f).pin_memory()
+            uh = torch.empty(N, dtype=torch.float64).pin_memory()
+            gh = torch.empty(2, N, dtype=torch.float64).pin_memory()
+            V.vp_eval_host(vp.tree, fh, uh, gh)
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                V.vp_eval_host(vp.tree, fh, uh, gh)
+            torch.cuda.synchronize()
+            e2e = {"value": world * N * args.steps / (time.perf_counter() - t0), "unit": "nodes/s",
+                   "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 24 * N}
+
+        near_ms = statistics.mean(m[4] for m in stage_ms)
+        near_flops = stage_flops[4]
+        if prec == V.VP_PREC_FP64:
+            achieved = near_flops / (near_ms / 1000.0) / 1e12
+            peak = N_SM * 2070.0e6 * FP64_FLOPS_PER_CLK_PER_SM / 1e12
+            roof = {"kernel": "k_gemm_gather_f64<1> (near-field tables)", "bound": "alu",
+                    "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk (derived; 1.20 TFLOP/s measured)"}
+            traffic = TRAFFIC_FP64_NEAR if (args.max_depth == 10 and args.alpha == 300.0) else None
+        else:
+            # tensor work: S(S+1)/2 slice products of the same shape as the FP64 contraction
+            slices = 6  # kSplitSlices in the library
+            achieved = near_flops * slices * (slices + 1) / 2 / (near_ms / 1000.0) / 1e12
+            peak = measured_peaks().get("bf16_tflops", 1900.0)
+            roof = {"kernel": "split-precision near-field GEMM (6 bf16 slices, fp32 accumulation; engine per launch)",
+                    "bound": "tensor", "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured",
+                    "fp64_equivalent_tflops": near_flops / (near_ms / 1000.0) / 1e12}
+            traffic = None
+        return {"value": value, "total_ms": total_ms, "N": N, "setup_s": setup_s, "n_tc": n_tc,
+                "launches": int(launches), "e2e": e2e, "clocks": sampler.summary(),
+                "stage_ms": {name: round(statistics.mean(m[k] for m in stage_ms), 4)
+                             for k, name in enumerate(V.STAGE_NAMES)},
+                "roofline": dict(roof, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                                 traffic=traffic)}
+    finally:
+        vp.close()
 
 
 def main():
@@ -372,88 +492,10 @@ def main():
     torch.cuda.set_device(local)
     B.build()
     w = workload(args.alpha, args.max_depth)
-    prec = V.VP_PREC_SPLIT if args.precision == "split" else V.VP_PREC_FP64
-    t0 = time.perf_counter()
-    vp = V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, order=args.order, precision=prec)
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
-    N = vp.N
-    f = torch.from_numpy(w.f).cuda()
-    u = torch.empty(N, dtype=torch.float64, device="cuda")
-    g = torch.empty(2, N, dtype=torch.float64, device="cuda")
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    launches, stage_flops = V.vp_tree_stats(vp.tree)
-    stream = torch.cuda.current_stream()
-    n_tc = choose_engine(V, args, vp.tree, f, u, g)
-
-    for _ in range(args.warmup):
-        V.vp_eval(vp.tree, f, u, g)
-    torch.cuda.synchronize()
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    stage_ms = []
-    step_ms = []
-    sampler = ClockSampler(local)
-    barrier()
-    with sampler:
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ms = V.vp_eval_timed(vp.tree, f, u, g)
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            stage_ms.append(ms)
-    barrier()
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * N * args.steps / (total_ms / 1000.0)
-
-    # e2e: host buffers, copies inside the timed region
-    e2e_value = None
-    if not args.no_e2e:
-        fh = torch.from_numpy(w.f).pin_memory()
-        uh = torch.empty(N, dtype=torch.float64).pin_memory()
-        gh = torch.empty(2, N, dtype=torch.float64).pin_memory()
-        V.vp_eval_host(vp.tree, fh, uh, gh)
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            V.vp_eval_host(vp.tree, fh, uh, gh)
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        e2e_value = world * N * args.steps / e2e_s
-
-    clocks = sampler.summary()
-    near_ms = statistics.mean(m[4] for m in stage_ms)
-    near_flops = stage_flops[4]
-    if prec == V.VP_PREC_FP64:
-        achieved = near_flops / (near_ms / 1000.0) / 1e12
-        peak = N_SM * 2070.0e6 * FP64_FLOPS_PER_CLK_PER_SM / 1e12
-        roof = {"kernel": "k_gemm_gather_f64<1> (near-field tables)", "bound": "alu",
-                "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk (derived; 1.20 TFLOP/s measured)"}
-    else:
-        # tensor work: S(S+1)/2 slice products of the same shape as the FP64 contraction
-        slices = 6  # kSplitSlices in the library
-        achieved = near_flops * slices * (slices + 1) / 2 / (near_ms / 1000.0) / 1e12
-        peak = measured_peaks().get("bf16_tflops", 1900.0)
-        roof = {"kernel": "split-precision near-field GEMM (6 fp16 slices, fp32 accumulation; engine per launch)",
-                "bound": "tensor",
-                "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json; fp16 has the same nominal rate)",
-                "fp64_equivalent_tflops": near_flops / (near_ms / 1000.0) / 1e12}
-    stages = {name: round(statistics.mean(m[k] for m in stage_ms), 4) for k, name in enumerate(V.STAGE_NAMES)}
+    # headline form: split precision unless only FP64 is asked for; "both" adds the FP64 form beside it
+    head_prec = V.VP_PREC_FP64 if args.precision == "fp64" else V.VP_PREC_SPLIT
+    head = measure(args, V, w, head_prec, world, local, not args.no_e2e)
+    plain = measure(args, V, w, V.VP_PREC_FP64, world, local, False) if args.precision == "both" else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -462,28 +504,31 @@ def main():
                "sample": f"{n} random target nodes of the same workload, {dt:.1f} s on {cores} threads"}
 
     if rank == 0:
+        split = head_prec == V.VP_PREC_SPLIT
         line = {"metric": "volume-potential leaf-nodes/s at stated rel err, split/batched vs plain FP64",
-                "value": value, "unit": "nodes/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if prec == V.VP_PREC_FP64 else "f64+f16-slices",
+                "value": head["value"], "unit": "nodes/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64+bf16-slices" if split else "f64",
                 "data": "synthetic",
-                "config": dict(workload_desc(w), precision=args.precision, order=args.order,
-                               engine=args.engine if prec == V.VP_PREC_SPLIT else "fp64",
-                               tcgen05_launches=n_tc,
+                "config": dict(workload_desc(w), precision="split" if split else "fp64", order=args.order,
+                               stated_rel_err=1e-9 if split else 1e-10,
+                               engine=args.engine if split else "fp64", tcgen05_launches=head["n_tc"],
                                l2="flushed before every timed step (512 MB write)",
                                parallelism="replicas" if world > 1 else "single GPU",
-                               setup_s=round(setup_s, 2)),
-                "stage_ms": stages,
-                "roofline": dict(roof, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                                 traffic=(TRAFFIC_FP64_NEAR if (prec == V.VP_PREC_FP64 and args.max_depth == 10
-                                                                and args.alpha == 300.0) else None)),
+                               setup_s=round(head["setup_s"], 2)),
+                "stage_ms": head["stage_ms"],
+                "roofline": head["roofline"],
                 "cpu_baseline": cpu,
-                "e2e": None if e2e_value is None else {"value": e2e_value, "unit": "nodes/s",
-                                                       "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 24 * N},
-                "gpu_launches": int(launches) * args.steps,
-                "clocks": clocks}
+                "e2e": head["e2e"],
+                "gpu_launches": head["launches"] * args.steps,
+                "clocks": head["clocks"]}
+        if plain is not None:
+            line["plain_fp64"] = {"value": plain["value"], "unit": "nodes/s",
+                                  "ms_per_step": plain["total_ms"] / args.steps, "stage_ms": plain["stage_ms"],
+                                  "roofline": plain["roofline"], "clocks": plain["clocks"],
+                                  "gpu_launches": plain["launches"] * args.steps}
+            line["split_speedup_vs_fp64"] = head["value"] / plain["value"]
         print(json.dumps(line), flush=True)
-    vp.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
