@@ -298,25 +298,31 @@ size_t mma_smem_bytes(int S) { return (size_t)2 * S * (kSplitBM + kMBN) * kMPitc
 
 // ------------------------------------------------------------------ engine 1: tcgen05
 //
-// One thread issues tcgen05.mma (kind::f16 with bf16 operands, M = 128, N = 128, K = 16) from
-// shared-memory descriptors into four fp32 accumulators in tensor memory (one per weight group);
-// operand tiles for one K step of 16 are staged by cp.async into a 4-stage ring in the canonical
-// K-major layout without swizzle (8 x 16-byte core matrices; the next core matrix along K is 128
-// bytes further, the next 8-row group 256 bytes further); tcgen05.commit arrives on the stage's
-// mbarrier when its MMAs are done, which frees the stage for the load three steps ahead. Every
-// mbarrier wait is bounded: on timeout the kernel raises a flag, waits (bounded) for its MMAs and
-// releases its tensor memory before returning.
+// Warp-specialised: warps 0-3 (128 threads) stage the operand tiles of each K step of 16 with
+// cp.async into a 4-stage ring in the canonical K-major layout without swizzle (8 x 16-byte core
+// matrices; the next core matrix along K is 128 bytes further, the next 8-row group 256 bytes
+// further) and, once their copies of a step have landed, arrive on that stage's `full` mbarrier;
+// warp 4 waits on it and one thread issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
+// N = 128, K = 16) into four fp32 accumulators in tensor memory (one per weight group), then
+// tcgen05.commit arrives on the stage's `empty` mbarrier, which lets the producers refill it.
+// After the last step a commit on `acc` releases the epilogue (warps 0-3, one accumulator row per
+// thread = one tensor-memory lane). Every wait is bounded and also ends when another thread has
+// given up; a kernel that gave up raises a flag, lets its issued MMAs finish (bounded), skips its
+// stores and releases its tensor memory.
 
 __device__ int g_split_error = 0;
 
-constexpr int kTcThreads = 128;
+constexpr int kTcProducers = 128;
+constexpr int kTcThreads = kTcProducers + 32;
 constexpr int kTcN = kSplitBN[kEngineTcgen05];   // 128
 constexpr int kTcKC = 16;                         // K per stage
 constexpr int kTcStages = 4;
+constexpr int kTcLag = 2;                         // cp.async groups a producer keeps in flight
 constexpr int kTcCols = kAcc * kTcN;              // 512 tensor-memory columns
 constexpr int kTcA = kSplitBM * kTcKC;            // elements per A slice tile
 constexpr int kTcB = kTcN * kTcKC;                // elements per B slice tile
 static_assert(kTcCols <= 512, "tensor memory holds 512 columns");
+static_assert(kSplitBM == 128 && kTcN == 128 && kTcProducers == 128, "producer thread mapping");
 
 __device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -329,8 +335,13 @@ __device__ inline void mbar_init(unsigned long long* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Bounded wait for the completion of phase `parity` of an mbarrier; false if it gave up (~2 s).
-__device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity) {
+__device__ inline void mbar_arrive(unsigned long long* bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the completion of phase `parity` of an mbarrier: false if it gave up (~2 s) or
+// if *abort became nonzero meanwhile.
+__device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int* abort = nullptr) {
   const unsigned a = smem_u32(bar);
   const long long t0 = clock64();
   while (true) {
@@ -338,8 +349,10 @@ __device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity) {
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(a), "r"(parity));
+        : "r"(a), "r"(parity)
+        : "memory");
     if (done) return true;
+    if (abort && *abort) return false;
     if (clock64() - t0 > 4000000000ll) return false;
   }
 }
@@ -349,22 +362,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
   extern __shared__ __align__(16) unsigned char smem_tc[];
   slice_t* As = reinterpret_cast<slice_t*>(smem_tc);  // [stages][S][kTcA]
   slice_t* Bs = As + kTcStages * S * kTcA;              // [stages][S][kTcB]
-  __shared__ __align__(8) unsigned long long mbar[kTcStages];
+  __shared__ __align__(8) unsigned long long full[kTcStages], empty[kTcStages], accbar;
   __shared__ unsigned tmem_base_sh;
-  __shared__ int abort_sh;
+  __shared__ volatile int abort_sh;
+  __shared__ long long col_dst[kTcN];  // per column: destination offset and source-vector exponent
+  __shared__ int col_e[kTcN];
   const SplitTile tile = a.tiles[blockIdx.x];
   const long long mat = a.a_mat[tile.group];
   const slice_t* Ag = a.A + mat * (long long)S * a.M * a.Kpad;
   const int* ea = a.ea + mat * a.M;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 0) {
+  if (warp == 4) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_sh)),
                  "n"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s) mbar_init(&mbar[s], 1);
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&full[s], kTcProducers);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accbar, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n");
   }
@@ -373,124 +392,150 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const unsigned tmem = tmem_base_sh;
   const int nk = a.Kpad / kTcKC;
-
-  // one cp.async group per K step (empty beyond the end, so that group counting stays uniform)
-  auto load_step = [&](int k) {
-    if (k < nk) {
-      const int st = k % kTcStages, k0 = k * kTcKC;
-      for (int e = tid; e < S * kSplitBM * 2; e += kTcThreads) {
-        const int sl = e / (kSplitBM * 2), rem = e % (kSplitBM * 2);
-        const int r = rem >> 1, c = rem & 1;
-        const int gr = tile.m0 + r;
-        const bool ok = gr < a.M;
-        const slice_t* src = Ag + ((long long)sl * a.M + (ok ? gr : 0)) * a.Kpad + k0 + c * 8;
-        slice_t* dst = As + (st * S + sl) * kTcA + ((r >> 3) * 2 + c) * 64 + (r & 7) * 8;
-        cp_async16(dst, src, ok);
-      }
-      for (int e = tid; e < S * kTcN * 2; e += kTcThreads) {
-        const int sl = e / (kTcN * 2), rem = e % (kTcN * 2);
-        const int col = rem >> 1, c = rem & 1;
-        const bool ok = col < tile.ncol;
-        const long long v = ok ? a.src_vec[tile.col0 + col] : 0;
-        const slice_t* src = a.B + (v * S + sl) * (long long)a.Kpad + k0 + c * 8;
-        slice_t* dst = Bs + (st * S + sl) * kTcB + ((col >> 3) * 2 + c) * 64 + (col & 7) * 8;
-        cp_async16(dst, src, ok);
-      }
-    }
-    cp_async_commit();
-  };
-
-  // instruction descriptor: D f32, A and B bf16, both K-major, N = 128, M = 128
-  const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcN >> 3) << 17) |
-                         ((unsigned)(kSplitBM >> 4) << 24);
   bool ok = true;
-  for (int k = 0; k < kTcStages - 1; ++k) load_step(k);
-  for (int k = 0; k < nk && ok; ++k) {
-    const int st = k % kTcStages;
-    cp_async_wait<kTcStages - 2>();  // the group of step k has landed
-    asm volatile("fence.proxy.async.shared::cta;\n");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const unsigned abase = smem_u32(As + st * S * kTcA), bbase = smem_u32(Bs + st * S * kTcB);
+
+  if (warp < 4) {
+    // ---- producers: thread t copies rows / columns (t >> 1) and (t >> 1) + 64, 16-byte chunk t & 1
+    const int c = tid & 1, r0 = tid >> 1;
+    const slice_t* asrc[2];
+    const slice_t* bsrc[2];
+    bool aok[2], bok[2];
+    int doff[2];
 #pragma unroll
-      for (int i = 0; i < S; ++i) {
-        const unsigned long long da = umma_desc(abase + i * kTcA * 2, 128, 256);
+    for (int h = 0; h < 2; ++h) {
+      const int r = r0 + 64 * h;
+      const int gr = tile.m0 + r;
+      aok[h] = gr < a.M;
+      asrc[h] = Ag + (long long)(aok[h] ? gr : 0) * a.Kpad + c * 8;
+      bok[h] = r < tile.ncol;
+      const long long v = bok[h] ? a.src_vec[tile.col0 + r] : 0;
+      bsrc[h] = a.B + v * S * (long long)a.Kpad + c * 8;
+      doff[h] = ((r >> 3) * 2 + c) * 64 + (r & 7) * 8;
+      if (c == 0) {
+        col_dst[r] = bok[h] ? a.dst_off[tile.col0 + r] : 0;
+        col_e[r] = bok[h] ? a.eb[v] : 0;
+      }
+    }
+    asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProducers) : "memory");  // column metadata visible to warps 0-3
+    const long long aslice = (long long)a.M * a.Kpad;
+    for (int k = 0; k < nk; ++k) {
+      const int st = k % kTcStages;
+      if (k >= kTcStages && !mbar_wait(&empty[st], ((k / kTcStages) - 1) & 1, &abort_sh)) {
+        ok = false;
+        break;
+      }
+      const int k0 = k * kTcKC;
 #pragma unroll
-        for (int j = 0; i + j < S; ++j) {
-          const unsigned long long db = umma_desc(bbase + j * kTcB * 2, 128, 256);
-          const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
-          const unsigned d_tmem = tmem + (unsigned)(w * kTcN);
-          // the first product of each accumulator (step 0, i = 0, j = w) overwrites it
-          const unsigned accum = (k == 0 && i == 0 && j == w) ? 0u : 1u;
-          asm volatile(
-              "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-              "l"(da), "l"(db), "r"(idesc), "r"(accum));
+      for (int sl = 0; sl < S; ++sl) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          cp_async16(As + (st * S + sl) * kTcA + doff[h], asrc[h] + sl * aslice + k0, aok[h]);
+          cp_async16(Bs + (st * S + sl) * kTcB + doff[h], bsrc[h] + (long long)sl * a.Kpad + k0, bok[h]);
         }
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_u32(&mbar[st])));
+      cp_async_commit();
+      if (k >= kTcLag) {
+        cp_async_wait<kTcLag>();  // the group of step k - kTcLag has landed
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive(&full[(k - kTcLag) % kTcStages]);
+      }
     }
-    // step k + stages - 1 goes into the stage of step k - 1 once the MMAs of step k - 1 are done
-    const int kn = k + kTcStages - 1;
-    if (k >= 1 && kn < nk) {
-      const int kp = k - 1;
-      if (!mbar_wait(&mbar[kp % kTcStages], (kp / kTcStages) & 1)) ok = false;
+    cp_async_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (ok) {
+      for (int k = (nk > kTcLag ? nk - kTcLag : 0); k < nk; ++k) mbar_arrive(&full[k % kTcStages]);
+    } else {
+      abort_sh = 1;
     }
-    if (ok) load_step(kn);
-    else cp_async_commit();
-    if (!ok) abort_sh = 1;
-    __syncthreads();
-    if (abort_sh) ok = false;
-  }
-  if (ok) {
-    const int last = nk - 1;
-    if (!mbar_wait(&mbar[last % kTcStages], (last / kTcStages) & 1)) ok = false;
-  }
-  cp_async_wait<0>();
-  if (!ok) {
-    if (tid == 0) atomicExch(&g_split_error, 1);
-    mbar_wait(&mbar[0], 0);
   } else {
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    const int row = tile.m0 + warp * 32 + lane;  // accumulator row = tensor-memory lane
-    const bool row_ok = row < a.M;
-    const int era = row_ok ? ea[row] : 0;
-#pragma unroll 1
-    for (int cb = 0; cb < kTcN / 16; ++cb) {
-      if (cb * 16 >= tile.ncol) break;
-      float v[kAcc][16];
+    // ---- MMA issuer (warp 4, one thread)
+    if (lane == 0) {
+      // instruction descriptor: D f32, A and B bf16, both K-major, N = 128, M = 128
+      const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcN >> 3) << 17) |
+                             ((unsigned)(kSplitBM >> 4) << 24);
+      for (int k = 0; k < nk; ++k) {
+        const int st = k % kTcStages;
+        if (!mbar_wait(&full[st], (k / kTcStages) & 1, &abort_sh)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+        const unsigned abase = smem_u32(As + st * S * kTcA), bbase = smem_u32(Bs + st * S * kTcB);
 #pragma unroll
-      for (int w = 0; w < kAcc; ++w) {
-        const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(w * kTcN + cb * 16);
-        unsigned r[16];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
+        for (int i = 0; i < S; ++i) {
+          const unsigned long long da = umma_desc(abase + i * kTcA * 2, 128, 256);
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[w][c] = __uint_as_float(r[c]);
+          for (int j = 0; i + j < S; ++j) {
+            const unsigned long long db = umma_desc(bbase + j * kTcB * 2, 128, 256);
+            const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
+            const unsigned d_tmem = tmem + (unsigned)(w * kTcN);
+            // the first product of each accumulator (step 0, i = 0, j = w) overwrites it
+            const unsigned accum = (k == 0 && i == 0 && j == w) ? 0u : 1u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                "l"(da), "l"(db), "r"(idesc), "r"(accum));
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(&empty[st])));
       }
-      asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-      if (row_ok) {
+      if (!ok) abort_sh = 1;
+      // arrives once every MMA issued above has completed (also after giving up)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_u32(&accbar)));
+    }
+  }
+
+  // ---- epilogue (warps 0-3): accumulator row = tensor-memory lane
+  if (warp < 4) {
+    const bool acc_ok = mbar_wait(&accbar, 0);
+    // warp-uniform decision (tcgen05.ld is a .sync.aligned warp instruction)
+    const bool go = __all_sync(0xffffffffu, acc_ok && !abort_sh);
+    if (!acc_ok) abort_sh = 1;
+    if (go) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      const int row = tile.m0 + warp * 32 + lane;
+      const bool row_ok = row < a.M;
+      const int era = row_ok ? ea[row] : 0;
+#pragma unroll 1
+      for (int cb = 0; cb < kTcN / 16; ++cb) {
+        if (cb * 16 >= tile.ncol) break;
+        float v[kAcc][16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int col = cb * 16 + c;
-          if (col >= tile.ncol) break;
-          float h = 0.f, l = 0.f;
+        for (int w = 0; w < kAcc; ++w) {
+          const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(w * kTcN + cb * 16);
+          unsigned r[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];\n"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
 #pragma unroll
-          for (int w = 0; w < kAcc; ++w) df_add(h, l, v[w][c]);
-          const long long vid = a.src_vec[tile.col0 + col];
-          store_out(a, a.dst_off[tile.col0 + col], row, h, l, era + a.eb[vid]);
+          for (int c = 0; c < 16; ++c) v[w][c] = __uint_as_float(r[c]);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+        if (row_ok) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int col = cb * 16 + c;
+            if (col >= tile.ncol) break;
+            float h = 0.f, l = 0.f;
+#pragma unroll
+            for (int w = 0; w < kAcc; ++w) df_add(h, l, v[w][c]);
+            store_out(a, col_dst[col], row, h, l, era + col_e[col]);
+          }
         }
       }
     }
   }
+  __syncthreads();
+  if (tid == 0 && abort_sh) atomicExch(&g_split_error, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 4) {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(kTcCols));
   }
 }
