@@ -138,15 +138,27 @@ __device__ inline void df_add(float& hi, float& lo, float x) {
   hi = t;
 }
 
+// 2^e as a float / double (e in the normal range of the type).
+__device__ inline float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+__device__ inline double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
 // Store one output element: double-float (h, l) times 2^e, as a double-float slot or into FP64.
+// Scaling by a power of two is exact (ldexp only where 2^e itself is not a normal number).
 __device__ inline void store_out(const SplitArgs& a, long long dst, int row, float h, float l, int e) {
   if (a.out_mode == 0) {
     float2 o;
-    o.x = ldexpf(h, e);
-    o.y = ldexpf(l, e);
+    if (e >= -126 && e <= 127) {
+      const float sc = pow2f(e);
+      o.x = h * sc;
+      o.y = l * sc;
+    } else {
+      o.x = ldexpf(h, e);
+      o.y = ldexpf(l, e);
+    }
     reinterpret_cast<float2*>(a.Y)[dst + row] = o;
   } else {
-    const double val = ldexp((double)h + (double)l, e);
+    const double hl = (double)h + (double)l;
+    const double val = (e >= -1022 && e <= 1023) ? hl * pow2d(e) : ldexp(hl, e);
     double* y = reinterpret_cast<double*>(a.Y) + dst + row;
     *y = (a.out_mode == 2) ? *y + val : val;
   }
@@ -298,21 +310,22 @@ size_t mma_smem_bytes(int S) { return (size_t)2 * S * (kSplitBM + kMBN) * kMPitc
 
 // ------------------------------------------------------------------ engine 1: tcgen05
 //
-// Warp-specialised: warps 0-3 (128 threads) stage the operand tiles of each K step of 16 with
+// Warp-specialised: warps 0-7 (256 threads) stage the operand tiles of each K step of 16 with
 // cp.async into a 4-stage ring in the canonical K-major layout without swizzle (8 x 16-byte core
 // matrices; the next core matrix along K is 128 bytes further, the next 8-row group 256 bytes
 // further) and, once their copies of a step have landed, arrive on that stage's `full` mbarrier;
-// warp 4 waits on it and one thread issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
+// warp 8 waits on it and one thread issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
 // N = 128, K = 16) into four fp32 accumulators in tensor memory (one per weight group), then
 // tcgen05.commit arrives on the stage's `empty` mbarrier, which lets the producers refill it.
-// After the last step a commit on `acc` releases the epilogue (warps 0-3, one accumulator row per
-// thread = one tensor-memory lane). Every wait is bounded and also ends when another thread has
-// given up; a kernel that gave up raises a flag, lets its issued MMAs finish (bounded), skips its
+// After the last step a commit on `acc` releases the epilogue (warps 0-7; a warp reads the 32
+// tensor-memory lanes of its quarter, one accumulator row per thread, for half of the columns).
+// Every wait is bounded and also ends when another thread has given up; a kernel that gave up raises a flag, lets its issued MMAs finish (bounded), skips its
 // stores and releases its tensor memory.
 
 __device__ int g_split_error = 0;
 
-constexpr int kTcProducers = 128;
+constexpr int kTcProducers = 256;                 // warps 0-7: operand staging, then the epilogue
+constexpr int kTcMmaWarp = kTcProducers / 32;     // warp 8: tensor-memory allocation and MMA issue
 constexpr int kTcThreads = kTcProducers + 32;
 constexpr int kTcN = kSplitBN[kEngineTcgen05];   // 128
 constexpr int kTcKC = 16;                         // K per stage
@@ -322,7 +335,7 @@ constexpr int kTcCols = kAcc * kTcN;              // 512 tensor-memory columns
 constexpr int kTcA = kSplitBM * kTcKC;            // elements per A slice tile
 constexpr int kTcB = kTcN * kTcKC;                // elements per B slice tile
 static_assert(kTcCols <= 512, "tensor memory holds 512 columns");
-static_assert(kSplitBM == 128 && kTcN == 128 && kTcProducers == 128, "producer thread mapping");
+static_assert(kSplitBM == 128 && kTcN == 128 && kTcProducers == 256, "producer thread mapping");
 
 __device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -373,7 +386,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
   const int* ea = a.ea + mat * a.M;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  if (warp == 4) {
+  if (warp == kTcMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_base_sh)),
                  "n"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
@@ -394,16 +407,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
   const int nk = a.Kpad / kTcKC;
   bool ok = true;
 
-  if (warp < 4) {
-    // ---- producers: thread t copies rows / columns (t >> 1) and (t >> 1) + 64, 16-byte chunk t & 1
+  if (warp < kTcMmaWarp) {
+    // ---- producers: thread t copies row / column t >> 1 of every slice, 16-byte chunk t & 1
     const int c = tid & 1, r0 = tid >> 1;
-    const slice_t* asrc[2];
-    const slice_t* bsrc[2];
-    bool aok[2], bok[2];
-    int doff[2];
+    const slice_t* asrc[1];
+    const slice_t* bsrc[1];
+    bool aok[1], bok[1];
+    int doff[1];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int r = r0 + 64 * h;
+    for (int h = 0; h < 1; ++h) {
+      const int r = r0;
       const int gr = tile.m0 + r;
       aok[h] = gr < a.M;
       asrc[h] = Ag + (long long)(aok[h] ? gr : 0) * a.Kpad + c * 8;
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
         col_e[r] = bok[h] ? a.eb[v] : 0;
       }
     }
-    asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProducers) : "memory");  // column metadata visible to warps 0-3
+    asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProducers) : "memory");  // column metadata visible to warps 0-7
     const long long aslice = (long long)a.M * a.Kpad;
     for (int k = 0; k < nk; ++k) {
       const int st = k % kTcStages;
@@ -428,7 +441,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
 #pragma unroll
       for (int sl = 0; sl < S; ++sl) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < 1; ++h) {
           cp_async16(As + (st * S + sl) * kTcA + doff[h], asrc[h] + sl * aslice + k0, aok[h]);
           cp_async16(Bs + (st * S + sl) * kTcB + doff[h], bsrc[h] + (long long)sl * a.Kpad + k0, bok[h]);
         }
@@ -448,7 +461,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
       abort_sh = 1;
     }
   } else {
-    // ---- MMA issuer (warp 4, one thread)
+    // ---- MMA issuer (warp 8, one thread)
     if (lane == 0) {
       // instruction descriptor: D f32, A and B bf16, both K-major, N = 128, M = 128
       const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcN >> 3) << 17) |
@@ -487,24 +500,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
     }
   }
 
-  // ---- epilogue (warps 0-3): accumulator row = tensor-memory lane
-  if (warp < 4) {
+  // ---- epilogue (warps 0-7): warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its accumulator
+  // rows) for columns 64 (w / 4) .. + 63
+  if (warp < kTcMmaWarp) {
     const bool acc_ok = mbar_wait(&accbar, 0);
     // warp-uniform decision (tcgen05.ld is a .sync.aligned warp instruction)
     const bool go = __all_sync(0xffffffffu, acc_ok && !abort_sh);
     if (!acc_ok) abort_sh = 1;
     if (go) {
       asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const int row = tile.m0 + warp * 32 + lane;
+      const int q = warp & 3, half = warp >> 2;
+      const int row = tile.m0 + q * 32 + lane;
       const bool row_ok = row < a.M;
       const int era = row_ok ? ea[row] : 0;
 #pragma unroll 1
-      for (int cb = 0; cb < kTcN / 16; ++cb) {
+      for (int cb = half * 4; cb < half * 4 + 4; ++cb) {
         if (cb * 16 >= tile.ncol) break;
         float v[kAcc][16];
 #pragma unroll
         for (int w = 0; w < kAcc; ++w) {
-          const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(w * kTcN + cb * 16);
+          const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(w * kTcN + cb * 16);
           unsigned r[16];
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
@@ -521,9 +536,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
           for (int c = 0; c < 16; ++c) {
             const int col = cb * 16 + c;
             if (col >= tile.ncol) break;
-            float h = 0.f, l = 0.f;
+            float h = v[0][c], l = 0.f;
 #pragma unroll
-            for (int w = 0; w < kAcc; ++w) df_add(h, l, v[w][c]);
+            for (int w = 1; w < kAcc; ++w) df_add(h, l, v[w][c]);
             store_out(a, col_dst[col], row, h, l, era + col_e[col]);
           }
         }
@@ -534,7 +549,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
   if (tid == 0 && abort_sh) atomicExch(&g_split_error, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
-  if (warp == 4) {
+  if (warp == kTcMmaWarp) {
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(kTcCols));
   }
