@@ -310,23 +310,28 @@ size_t mma_smem_bytes(int S) { return (size_t)2 * S * (kSplitBM + kMBN) * kMPitc
 
 // ------------------------------------------------------------------ engine 1: tcgen05
 //
-// Warp-specialised: warps 0-7 (256 threads) stage the operand tiles of each K step of 16 with
-// cp.async into a 4-stage ring in the canonical K-major layout without swizzle (8 x 16-byte core
-// matrices; the next core matrix along K is 128 bytes further, the next 8-row group 256 bytes
-// further) and, once their copies of a step have landed, arrive on that stage's `full` mbarrier;
-// warp 8 waits on it and one thread issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
-// N = 128, K = 16) into four fp32 accumulators in tensor memory (one per weight group), then
-// tcgen05.commit arrives on the stage's `empty` mbarrier, which lets the producers refill it.
-// After the last step a commit on `acc` releases the epilogue (warps 0-7; a warp reads the 32
-// tensor-memory lanes of its quarter, one accumulator row per thread, for half of the columns).
-// Every wait is bounded and also ends when another thread has given up; a kernel that gave up raises a flag, lets its issued MMAs finish (bounded), skips its
-// stores and releases its tensor memory.
+// Persistent and warp-specialised: one CTA per SM walks the tile list (tile t, t + gridDim.x, ...).
+//  * warps 0-7 (producers) stage the operand tiles of every K step of 16 with cp.async into a
+//    4-stage ring in the canonical K-major layout without swizzle (8 x 16-byte core matrices; the
+//    next core matrix along K is 128 bytes further, the next 8-row group 256 bytes further); once
+//    their copies of a step have landed they arrive on the stage's `full` mbarrier. The ring runs
+//    on across tiles, so the next tile's operands stream in while the current one is drained.
+//  * warp 16 (one thread) waits on `full`, issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
+//    N = 128, K = 16) into four fp32 accumulators in tensor memory (one per weight group) and
+//    commits to the stage's `empty` mbarrier; after a tile's last step it commits to `acc`, and it
+//    starts the next tile once the epilogue has arrived on `tmem_free`.
+//  * warps 8-15 (epilogue) read the accumulators (warp w: tensor-memory lanes 32 (w % 4) .. + 31,
+//    one accumulator row per thread, half of the columns), fold them in double-float and store.
+// Every wait is bounded and also ends once another thread has given up; decisions taken by the
+// epilogue group are made uniform with a barrier reduction. A kernel that gave up raises a flag,
+// lets its issued MMAs finish (bounded), skips its remaining stores and releases tensor memory.
 
 __device__ int g_split_error = 0;
 
-constexpr int kTcProducers = 256;                 // warps 0-7: operand staging, then the epilogue
-constexpr int kTcMmaWarp = kTcProducers / 32;     // warp 8: tensor-memory allocation and MMA issue
-constexpr int kTcThreads = kTcProducers + 32;
+constexpr int kTcProducers = 256;                 // warps 0-7
+constexpr int kTcEpilogue = 256;                  // warps 8-15
+constexpr int kTcMmaWarp = (kTcProducers + kTcEpilogue) / 32;  // warp 16
+constexpr int kTcThreads = kTcProducers + kTcEpilogue + 32;
 constexpr int kTcN = kSplitBN[kEngineTcgen05];   // 128
 constexpr int kTcKC = 16;                         // K per stage
 constexpr int kTcStages = 4;
@@ -335,7 +340,7 @@ constexpr int kTcCols = kAcc * kTcN;              // 512 tensor-memory columns
 constexpr int kTcA = kSplitBM * kTcKC;            // elements per A slice tile
 constexpr int kTcB = kTcN * kTcKC;                // elements per B slice tile
 static_assert(kTcCols <= 512, "tensor memory holds 512 columns");
-static_assert(kSplitBM == 128 && kTcN == 128 && kTcProducers == 256, "producer thread mapping");
+static_assert(kSplitBM == 128 && kTcN == 128 && kTcProducers == 256 && kTcEpilogue == 256, "thread mapping");
 
 __device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -350,6 +355,11 @@ __device__ inline void mbar_init(unsigned long long* bar, unsigned count) {
 
 __device__ inline void mbar_arrive(unsigned long long* bar) {
   asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ inline void umma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
 }
 
 // Bounded wait for the completion of phase `parity` of an mbarrier: false if it gave up (~2 s) or
@@ -370,20 +380,27 @@ __device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity, volat
   }
 }
 
+// Named barrier 1 over the epilogue warps, returning the AND of `pred` over them (uniform).
+__device__ inline bool epi_all(bool pred) {
+  unsigned r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, 1, %2, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)pred), "n"(kTcEpilogue)
+      : "memory");
+  return r != 0;
+}
+
 template <int S>
-__global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a, int n_tiles) {
   extern __shared__ __align__(16) unsigned char smem_tc[];
   slice_t* As = reinterpret_cast<slice_t*>(smem_tc);  // [stages][S][kTcA]
   slice_t* Bs = As + kTcStages * S * kTcA;              // [stages][S][kTcB]
-  __shared__ __align__(8) unsigned long long full[kTcStages], empty[kTcStages], accbar;
+  __shared__ __align__(8) unsigned long long full[kTcStages], empty[kTcStages], accbar, tmem_free, donebar;
   __shared__ unsigned tmem_base_sh;
   __shared__ volatile int abort_sh;
-  __shared__ long long col_dst[kTcN];  // per column: destination offset and source-vector exponent
+  __shared__ long long col_dst[kTcN];  // current tile, per column: destination offset, source exponent
   __shared__ int col_e[kTcN];
-  const SplitTile tile = a.tiles[blockIdx.x];
-  const long long mat = a.a_mat[tile.group];
-  const slice_t* Ag = a.A + mat * (long long)S * a.M * a.Kpad;
-  const int* ea = a.ea + mat * a.M;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == kTcMmaWarp) {
@@ -397,6 +414,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
       mbar_init(&empty[s], 1);
     }
     mbar_init(&accbar, 1);
+    mbar_init(&tmem_free, kTcEpilogue);
+    mbar_init(&donebar, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n");
   }
@@ -405,70 +424,128 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const unsigned tmem = tmem_base_sh;
   const int nk = a.Kpad / kTcKC;
-  bool ok = true;
 
-  if (warp < kTcMmaWarp) {
+  if (warp < kTcProducers / 32) {
     // ---- producers: thread t copies row / column t >> 1 of every slice, 16-byte chunk t & 1
-    const int c = tid & 1, r0 = tid >> 1;
-    const slice_t* asrc[1];
-    const slice_t* bsrc[1];
-    bool aok[1], bok[1];
-    int doff[1];
-#pragma unroll
-    for (int h = 0; h < 1; ++h) {
-      const int r = r0;
-      const int gr = tile.m0 + r;
-      aok[h] = gr < a.M;
-      asrc[h] = Ag + (long long)(aok[h] ? gr : 0) * a.Kpad + c * 8;
-      bok[h] = r < tile.ncol;
-      const long long v = bok[h] ? a.src_vec[tile.col0 + r] : 0;
-      bsrc[h] = a.B + v * S * (long long)a.Kpad + c * 8;
-      doff[h] = ((r >> 3) * 2 + c) * 64 + (r & 7) * 8;
-      if (c == 0) {
-        col_dst[r] = bok[h] ? a.dst_off[tile.col0 + r] : 0;
-        col_e[r] = bok[h] ? a.eb[v] : 0;
-      }
-    }
-    asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProducers) : "memory");  // column metadata visible to warps 0-7
+    const int c = tid & 1, r = tid >> 1;
+    const int doff = ((r >> 3) * 2 + c) * 64 + (r & 7) * 8;
     const long long aslice = (long long)a.M * a.Kpad;
-    for (int k = 0; k < nk; ++k) {
-      const int st = k % kTcStages;
-      if (k >= kTcStages && !mbar_wait(&empty[st], ((k / kTcStages) - 1) & 1, &abort_sh)) {
-        ok = false;
-        break;
-      }
-      const int k0 = k * kTcKC;
-#pragma unroll
-      for (int sl = 0; sl < S; ++sl) {
-#pragma unroll
-        for (int h = 0; h < 1; ++h) {
-          cp_async16(As + (st * S + sl) * kTcA + doff[h], asrc[h] + sl * aslice + k0, aok[h]);
-          cp_async16(Bs + (st * S + sl) * kTcB + doff[h], bsrc[h] + (long long)sl * a.Kpad + k0, bok[h]);
+    long long g = 0;  // ring step across tiles
+    bool ok = true;
+    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+      const SplitTile tile = a.tiles[t];
+      const int gr = tile.m0 + r;
+      const bool aok = gr < a.M;
+      const slice_t* asrc = a.A + a.a_mat[tile.group] * (long long)S * aslice + (long long)(aok ? gr : 0) * a.Kpad +
+                            c * 8;
+      const bool bok = r < tile.ncol;
+      const long long v = bok ? a.src_vec[tile.col0 + r] : 0;
+      const slice_t* bsrc = a.B + v * S * (long long)a.Kpad + c * 8;
+      for (int k = 0; k < nk; ++k, ++g) {
+        const int st = (int)(g % kTcStages);
+        if (g >= kTcStages && !mbar_wait(&empty[st], (unsigned)((g / kTcStages) - 1) & 1u, &abort_sh)) {
+          ok = false;
+          break;
         }
-      }
-      cp_async_commit();
-      if (k >= kTcLag) {
-        cp_async_wait<kTcLag>();  // the group of step k - kTcLag has landed
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        mbar_arrive(&full[(k - kTcLag) % kTcStages]);
+        const int k0 = k * kTcKC;
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+          cp_async16(As + (st * S + sl) * kTcA + doff, asrc + sl * aslice + k0, aok);
+          cp_async16(Bs + (st * S + sl) * kTcB + doff, bsrc + (long long)sl * a.Kpad + k0, bok);
+        }
+        cp_async_commit();
+        if (g >= kTcLag) {
+          cp_async_wait<kTcLag>();  // the group of step g - kTcLag has landed
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          mbar_arrive(&full[(g - kTcLag) % kTcStages]);
+        }
       }
     }
     cp_async_wait<0>();
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     if (ok) {
-      for (int k = (nk > kTcLag ? nk - kTcLag : 0); k < nk; ++k) mbar_arrive(&full[k % kTcStages]);
+      for (long long q = (g > kTcLag ? g - kTcLag : 0); q < g; ++q) mbar_arrive(&full[q % kTcStages]);
     } else {
       abort_sh = 1;
     }
-  } else {
-    // ---- MMA issuer (warp 8, one thread)
-    if (lane == 0) {
-      // instruction descriptor: D f32, A and B bf16, both K-major, N = 128, M = 128
-      const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcN >> 3) << 17) |
-                             ((unsigned)(kSplitBM >> 4) << 24);
-      for (int k = 0; k < nk; ++k) {
-        const int st = k % kTcStages;
-        if (!mbar_wait(&full[st], (k / kTcStages) & 1, &abort_sh)) {
+  } else if (warp < kTcMmaWarp) {
+    // ---- epilogue
+    const int e = tid - kTcProducers;
+    const int q = warp & 3, half = (warp - kTcProducers / 32) >> 2;
+    int it = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+      const SplitTile tile = a.tiles[t];
+      if ((e & 1) == 0) {
+        const int col = e >> 1;
+        const bool cok = col < tile.ncol;
+        const long long v = cok ? a.src_vec[tile.col0 + col] : 0;
+        col_dst[col] = cok ? a.dst_off[tile.col0 + col] : 0;
+        col_e[col] = cok ? a.eb[v] : 0;
+      }
+      const int row = tile.m0 + q * 32 + lane;
+      const bool row_ok = row < a.M;
+      const int era = row_ok ? a.ea[a.a_mat[tile.group] * a.M + row] : 0;
+      const bool acc_ok = mbar_wait(&accbar, (unsigned)it & 1u, &abort_sh);
+      // uniform over the epilogue group (also publishes the column metadata written above)
+      if (!epi_all(acc_ok && !abort_sh)) {
+        abort_sh = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+#pragma unroll 1
+      for (int cb = half * 4; cb < half * 4 + 4; ++cb) {
+        if (cb * 16 >= tile.ncol) break;
+        float vv[kAcc][16];
+#pragma unroll
+        for (int w = 0; w < kAcc; ++w) {
+          const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(w * kTcN + cb * 16);
+          unsigned rr[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+              "[%16];\n"
+              : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+                "=r"(rr[14]), "=r"(rr[15])
+              : "r"(taddr));
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) vv[w][cc] = __uint_as_float(rr[cc]);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+        if (row_ok) {
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const int col = cb * 16 + cc;
+            if (col >= tile.ncol) break;
+            float h = vv[0][cc], l = 0.f;
+#pragma unroll
+            for (int w = 1; w < kAcc; ++w) df_add(h, l, vv[w][cc]);
+            store_out(a, col_dst[col], row, h, l, era + col_e[col]);
+          }
+        }
+      }
+      // accumulators read: the MMA warp may start the next tile
+      asm volatile("tcgen05.fence::before_thread_sync;\n");
+      mbar_arrive(&tmem_free);
+      // column metadata of this tile no longer needed by any epilogue thread
+      asm volatile("bar.sync 1, %0;\n" ::"n"(kTcEpilogue) : "memory");
+    }
+  } else if (lane == 0) {
+    // ---- MMA issuer
+    // instruction descriptor: D f32, A and B bf16, both K-major, N = 128, M = 128
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcN >> 3) << 17) |
+                           ((unsigned)(kSplitBM >> 4) << 24);
+    long long g = 0;
+    bool ok = true;
+    int it = 0;
+    for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++it) {
+      if (it > 0 && !mbar_wait(&tmem_free, (unsigned)(it - 1) & 1u, &abort_sh)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;\n");
+      for (int k = 0; k < nk; ++k, ++g) {
+        const int st = (int)(g % kTcStages);
+        if (!mbar_wait(&full[st], (unsigned)(g / kTcStages) & 1u, &abort_sh)) {
           ok = false;
           break;
         }
@@ -482,7 +559,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
             const unsigned long long db = umma_desc(bbase + j * kTcB * 2, 128, 256);
             const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
             const unsigned d_tmem = tmem + (unsigned)(w * kTcN);
-            // the first product of each accumulator (step 0, i = 0, j = w) overwrites it
+            // the first product of each accumulator in a tile (step 0, i = 0, j = w) overwrites it
             const unsigned accum = (k == 0 && i == 0 && j == w) ? 0u : 1u;
             asm volatile(
                 "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -490,61 +567,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a) {
                 "l"(da), "l"(db), "r"(idesc), "r"(accum));
           }
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-            smem_u32(&empty[st])));
+        umma_commit(&empty[st]);
       }
-      if (!ok) abort_sh = 1;
-      // arrives once every MMA issued above has completed (also after giving up)
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_u32(&accbar)));
+      if (ok) umma_commit(&accbar);
     }
+    if (!ok) abort_sh = 1;
+    // every MMA issued above has completed once this arrives
+    umma_commit(&donebar);
+    mbar_wait(&donebar, 0);
   }
 
-  // ---- epilogue (warps 0-7): warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its accumulator
-  // rows) for columns 64 (w / 4) .. + 63
-  if (warp < kTcMmaWarp) {
-    const bool acc_ok = mbar_wait(&accbar, 0);
-    // warp-uniform decision (tcgen05.ld is a .sync.aligned warp instruction)
-    const bool go = __all_sync(0xffffffffu, acc_ok && !abort_sh);
-    if (!acc_ok) abort_sh = 1;
-    if (go) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const int q = warp & 3, half = warp >> 2;
-      const int row = tile.m0 + q * 32 + lane;
-      const bool row_ok = row < a.M;
-      const int era = row_ok ? ea[row] : 0;
-#pragma unroll 1
-      for (int cb = half * 4; cb < half * 4 + 4; ++cb) {
-        if (cb * 16 >= tile.ncol) break;
-        float v[kAcc][16];
-#pragma unroll
-        for (int w = 0; w < kAcc; ++w) {
-          const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(w * kTcN + cb * 16);
-          unsigned r[16];
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];\n"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-              : "r"(taddr));
-#pragma unroll
-          for (int c = 0; c < 16; ++c) v[w][c] = __uint_as_float(r[c]);
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-        if (row_ok) {
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int col = cb * 16 + c;
-            if (col >= tile.ncol) break;
-            float h = v[0][c], l = 0.f;
-#pragma unroll
-            for (int w = 1; w < kAcc; ++w) df_add(h, l, v[w][c]);
-            store_out(a, col_dst[col], row, h, l, era + col_e[col]);
-          }
-        }
-      }
-    }
-  }
   __syncthreads();
   if (tid == 0 && abort_sh) atomicExch(&g_split_error, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -636,6 +668,9 @@ void free_split_tables(vp_tables_s* T) {
   T->near_split = nullptr;
 }
 
+// Persistent tcgen05 grid: one CTA per SM of the device last prepared.
+int g_num_sms = 152;
+
 // Per device: allow the GEMM kernels their dynamic shared memory (call outside stream capture).
 int prepare_split_launch() {
   int dev = 0;
@@ -646,6 +681,9 @@ int prepare_split_launch() {
                            (int)mma_smem_bytes(kSplitSlices)));
   TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_bytes(kSplitSlices)));
+  int sms = 0;
+  TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  g_num_sms = sms > 0 ? sms : 1;
   if (dev >= 0 && dev < 64) done[dev] = true;
   return VP_OK;
 }
@@ -667,8 +705,10 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engin
     if (rc) return rc;
   }
   if (n_tiles <= 0) return VP_OK;
-  if (engine == kEngineTcgen05)
-    k_split_gemm_tc<kSplitSlices><<<n_tiles, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(a);
+  if (engine == kEngineTcgen05) {
+    const int grid = n_tiles < g_num_sms ? n_tiles : g_num_sms;
+    k_split_gemm_tc<kSplitSlices><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(a, n_tiles);
+  }
   else
     k_split_gemm<kSplitSlices><<<n_tiles, 256, mma_smem_bytes(kSplitSlices), s>>>(a);
   TRY(cudaGetLastError());
