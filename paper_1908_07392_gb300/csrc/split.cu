@@ -170,6 +170,7 @@ __device__ inline void cp_async16(void* smem, const void* gmem, bool valid) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(n));
 }
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 template <int N>
 __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
@@ -313,10 +314,12 @@ size_t mma_smem_bytes(int S) { return (size_t)2 * S * (kSplitBM + kMBN) * kMPitc
 // Persistent and warp-specialised: one CTA per SM walks the tile list (tile t, t + gridDim.x, ...).
 //  * warps 0-7 (producers) stage the operand tiles of every K step of 16 with cp.async into a
 //    4-stage ring in the canonical K-major layout without swizzle (8 x 16-byte core matrices; the
-//    next core matrix along K is 128 bytes further, the next 8-row group 256 bytes further); once
-//    their copies of a step have landed they arrive on the stage's `full` mbarrier. The ring runs
-//    on across tiles, so the next tile's operands stream in while the current one is drained.
-//  * warp 16 (one thread) waits on `full`, issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
+//    next core matrix along K is 128 bytes further, the next 8-row group 256 bytes further); each
+//    thread's copies arrive on the stage's `full` mbarrier when they land (cp.async.mbarrier.arrive),
+//    so a producer waits only for free stages. The ring runs on across tiles, so the next tile's
+//    operands stream in while the current one is drained.
+//  * warp 16 (one thread) waits on `full`, fences the generic-proxy writes of the stage against
+//    the async proxy, issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
 //    N = 128, K = 16) into four fp32 accumulators in tensor memory (one per weight group) and
 //    commits to the stage's `empty` mbarrier; after a tile's last step it commits to `acc`, and it
 //    starts the next tile once the epilogue has arrived on `tmem_free`.
@@ -335,7 +338,6 @@ constexpr int kTcThreads = kTcProducers + kTcEpilogue + 32;
 constexpr int kTcN = kSplitBN[kEngineTcgen05];   // 128
 constexpr int kTcKC = 16;                         // K per stage
 constexpr int kTcStages = 4;
-constexpr int kTcLag = 2;                         // cp.async groups a producer keeps in flight
 constexpr int kTcCols = kAcc * kTcN;              // 512 tensor-memory columns
 constexpr int kTcA = kSplitBM * kTcKC;            // elements per A slice tile
 constexpr int kTcB = kTcN * kTcKC;                // elements per B slice tile
@@ -453,21 +455,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a, in
           cp_async16(As + (st * S + sl) * kTcA + doff, asrc + sl * aslice + k0, aok);
           cp_async16(Bs + (st * S + sl) * kTcB + doff, bsrc + (long long)sl * a.Kpad + k0, bok);
         }
-        cp_async_commit();
-        if (g >= kTcLag) {
-          cp_async_wait<kTcLag>();  // the group of step g - kTcLag has landed
-          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-          mbar_arrive(&full[(g - kTcLag) % kTcStages]);
-        }
+        // arrives on full[st] once this thread's copies so far have landed; the thread moves on
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full[st])) : "memory");
       }
     }
-    cp_async_wait<0>();
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    if (ok) {
-      for (long long q = (g > kTcLag ? g - kTcLag : 0); q < g; ++q) mbar_arrive(&full[q % kTcStages]);
-    } else {
-      abort_sh = 1;
-    }
+    cp_async_wait_all();
+    if (!ok) abort_sh = 1;
   } else if (warp < kTcMmaWarp) {
     // ---- epilogue
     const int e = tid - kTcProducers;
@@ -549,6 +542,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a, in
           ok = false;
           break;
         }
+        // the stage was written through the generic proxy (cp.async); the MMA reads it through the async proxy
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const unsigned abase = smem_u32(As + st * S * kTcA), bbase = smem_u32(Bs + st * S * kTcB);
 #pragma unroll
