@@ -670,6 +670,7 @@ SplitArgs split_args(const vp_tree_s* tr, const DevSplit& d, double* const* bufs
   SplitArgs a = d.args;
   a.A = static_cast<const slice_t*>(tb->A);
   a.ea = tb->ea;
+  a.tmap = tb->tmap;
   a.B = static_cast<const slice_t*>(tr->sv[d.vec]);
   a.eb = tr->se[d.vec];
   a.Y = bufs[d.dst];

@@ -20,6 +20,7 @@
 //     2^(ea[r] + eb) exactly. Products with i + j > S - 1 are dropped.
 // Two engines run the same arithmetic: warp-level mma.sync (m16n8k16 bf16),
 // and tcgen05.mma with the accumulators in tensor memory.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -312,11 +313,13 @@ size_t mma_smem_bytes(int S) { return (size_t)2 * S * (kSplitBM + kMBN) * kMPitc
 // ------------------------------------------------------------------ engine 1: tcgen05
 //
 // Persistent and warp-specialised: one CTA per SM walks the tile list (tile t, t + gridDim.x, ...).
-//  * warps 0-7 (producers) stage the operand tiles of every K step of 16 with cp.async into a
-//    4-stage ring in the canonical K-major layout without swizzle (8 x 16-byte core matrices; the
-//    next core matrix along K is 128 bytes further, the next 8-row group 256 bytes further); each
-//    thread's copies arrive on the stage's `full` mbarrier when they land (cp.async.mbarrier.arrive),
-//    so a producer waits only for free stages. The ring runs on across tiles, so the next tile's
+//  * warps 0-7 (producers) stage the operands of every K step of 16 into a 4-stage ring in the
+//    canonical K-major layout without swizzle (8-row x 16-byte core matrices): the operator slices
+//    (A) by TMA, one box per slice issued by thread 0 (next core matrix along K 2048 bytes further,
+//    next 8-row group 128 bytes further), the gathered source columns (B) by cp.async (128 and 256
+//    bytes); each thread's copies arrive on the stage's `full` mbarrier when they land
+//    (cp.async.mbarrier.arrive), the TMA boxes count their bytes on it, and a producer waits only
+//    for free stages. The ring runs on across tiles, so the next tile's
 //    operands stream in while the current one is drained.
 //  * warp 16 (one thread) waits on `full`, fences the generic-proxy writes of the stage against
 //    the async proxy, issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
@@ -394,11 +397,13 @@ __device__ inline bool epi_all(bool pred) {
 }
 
 template <int S>
-__global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a, int n_tiles) {
-  extern __shared__ __align__(16) unsigned char smem_tc[];
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_split_gemm_tc(SplitArgs a, int n_tiles, const __grid_constant__ CUtensorMap tmA) {
+  extern __shared__ __align__(128) unsigned char smem_tc[];
   slice_t* As = reinterpret_cast<slice_t*>(smem_tc);  // [stages][S][kTcA]
   slice_t* Bs = As + kTcStages * S * kTcA;              // [stages][S][kTcB]
-  __shared__ __align__(8) unsigned long long full[kTcStages], empty[kTcStages], accbar, tmem_free, donebar;
+  __shared__ __align__(8) unsigned long long full[kTcStages], fullA[kTcStages], empty[kTcStages], accbar, tmem_free,
+      donebar;
   __shared__ unsigned tmem_base_sh;
   __shared__ volatile int abort_sh;
   __shared__ long long col_dst[kTcN];  // current tile, per column: destination offset, source exponent
@@ -412,7 +417,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a, in
   }
   if (tid == 0) {
     for (int s = 0; s < kTcStages; ++s) {
-      mbar_init(&full[s], kTcProducers);
+      mbar_init(&full[s], kTcProducers);  // cp.async copies of the B operand
+      mbar_init(&fullA[s], 1);            // TMA boxes of the A operand (byte count)
       mbar_init(&empty[s], 1);
     }
     mbar_init(&accbar, 1);
@@ -431,15 +437,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a, in
     // ---- producers: thread t copies row / column t >> 1 of every slice, 16-byte chunk t & 1
     const int c = tid & 1, r = tid >> 1;
     const int doff = ((r >> 3) * 2 + c) * 64 + (r & 7) * 8;
-    const long long aslice = (long long)a.M * a.Kpad;
     long long g = 0;  // ring step across tiles
     bool ok = true;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const SplitTile tile = a.tiles[t];
-      const int gr = tile.m0 + r;
-      const bool aok = gr < a.M;
-      const slice_t* asrc = a.A + a.a_mat[tile.group] * (long long)S * aslice + (long long)(aok ? gr : 0) * a.Kpad +
-                            c * 8;
+      // A: slice sl of this tile is slice index mat S + sl of the tensor map, rows from m0
+      const int aslc = (int)(a.a_mat[tile.group] * S);
       const bool bok = r < tile.ncol;
       const long long v = bok ? a.src_vec[tile.col0 + r] : 0;
       const slice_t* bsrc = a.B + v * S * (long long)a.Kpad + c * 8;
@@ -450,17 +453,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a, in
           break;
         }
         const int k0 = k * kTcKC;
+        if (tid == 0) {
+          // A operand by TMA: one box per slice, completion counted in bytes on full[st]
+          asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
+                           smem_u32(&fullA[st])),
+                       "n"(S * kTcA * (int)sizeof(slice_t))
+                       : "memory");
 #pragma unroll
-        for (int sl = 0; sl < S; ++sl) {
-          cp_async16(As + (st * S + sl) * kTcA + doff, asrc + sl * aslice + k0, aok);
-          cp_async16(Bs + (st * S + sl) * kTcB + doff, bsrc + (long long)sl * a.Kpad + k0, bok);
+          for (int sl = 0; sl < S; ++sl)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes "
+                "[%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(As + (st * S + sl) * kTcA)),
+                "l"(reinterpret_cast<unsigned long long>(&tmA)), "r"(0), "r"(tile.m0), "r"(aslc + sl), "r"(k0 / 8),
+                "r"(smem_u32(&fullA[st]))
+                : "memory");
         }
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl)
+          cp_async16(Bs + (st * S + sl) * kTcB + doff, bsrc + (long long)sl * a.Kpad + k0, bok);
         // arrives on full[st] once this thread's copies so far have landed; the thread moves on
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full[st])) : "memory");
       }
     }
     cp_async_wait_all();
     if (!ok) abort_sh = 1;
+    if (tid == 0) {
+      // no TMA box may still be in flight when the CTA ends (after giving up too): wait for the
+      // boxes of the last stages issued (earlier ones were consumed by the MMA warp)
+      for (long long q = (g > kTcStages ? g - kTcStages : 0); q < g; ++q)
+        mbar_wait(&fullA[q % kTcStages], (unsigned)(q / kTcStages) & 1u);
+    }
   } else if (warp < kTcMmaWarp) {
     // ---- epilogue
     const int e = tid - kTcProducers;
@@ -538,17 +560,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_split_gemm_tc(SplitArgs a, in
       asm volatile("tcgen05.fence::after_thread_sync;\n");
       for (int k = 0; k < nk; ++k, ++g) {
         const int st = (int)(g % kTcStages);
-        if (!mbar_wait(&full[st], (unsigned)(g / kTcStages) & 1u, &abort_sh)) {
+        if (!mbar_wait(&full[st], (unsigned)(g / kTcStages) & 1u, &abort_sh) ||
+            !mbar_wait(&fullA[st], (unsigned)(g / kTcStages) & 1u, &abort_sh)) {
           ok = false;
           break;
         }
-        // the stage was written through the generic proxy (cp.async); the MMA reads it through the async proxy
+        // the B part of the stage was written through the generic proxy (cp.async); the MMA reads
+        // it through the async proxy
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::after_thread_sync;\n");
         const unsigned abase = smem_u32(As + st * S * kTcA), bbase = smem_u32(Bs + st * S * kTcB);
 #pragma unroll
         for (int i = 0; i < S; ++i) {
-          const unsigned long long da = umma_desc(abase + i * kTcA * 2, 128, 256);
+          // A (TMA layout): next core matrix along K 2048 bytes further, next 8-row group 128 bytes
+          const unsigned long long da = umma_desc(abase + i * kTcA * 2, 2048, 128);
 #pragma unroll
           for (int j = 0; i + j < S; ++j) {
             const unsigned long long db = umma_desc(bbase + j * kTcB * 2, 128, 256);
@@ -610,6 +635,35 @@ __global__ void k_reduce_df(DFReduceArgs a) {
   }
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map over the slices [nmat][S][M][Kpad] seen as a 4-D tensor (8 elements, M rows, nmat S
+// slices, K/8 chunks) with strides (2 B, 2 Kpad B, 2 M Kpad B, 16 B): a box {8, 128, 1, 2} is one K
+// step of 16 for 128 rows of one slice (rows past M read as zeros), stored in shared memory as
+// [chunk][row][8 elements], i.e. 8-row x 16-byte core matrices, the next core matrix along K 2048
+// bytes further and the next 8-row group 128 bytes further.
+int encode_slice_map(SplitTable* t, int S) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return VP_ERR_CUDA;
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const cuuint64_t row_bytes = (cuuint64_t)t->Kpad * sizeof(slice_t);
+  const cuuint64_t dims[4] = {8, (cuuint64_t)t->M, (cuuint64_t)t->nmat * S, (cuuint64_t)(t->Kpad / 8)};
+  const cuuint64_t strides[3] = {row_bytes, row_bytes * t->M, 16};
+  const cuuint32_t box[4] = {8, 128, 1, 2};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(reinterpret_cast<CUtensorMap*>(t->tmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, t->A, dims,
+                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? VP_OK : VP_ERR_CUDA;
+}
+
 constexpr int kKAlign = 32;  // padded K: a multiple of both engines' K steps
 int kpad(int K) { return (K + kKAlign - 1) / kKAlign * kKAlign; }
 
@@ -623,7 +677,7 @@ int slice_table(const double* A, int nmat, int M, int K, int lda, long long mstr
   k_slice_rows<kSplitSlices><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(A, mstride, lda, M, K, out->Kpad,
                                                                                  nmat, (slice_t*)out->A, out->ea);
   TRY(cudaGetLastError());
-  return VP_OK;
+  return encode_slice_map(out, S);
 }
 
 }  // namespace
@@ -702,7 +756,8 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engin
   if (n_tiles <= 0) return VP_OK;
   if (engine == kEngineTcgen05) {
     const int grid = n_tiles < g_num_sms ? n_tiles : g_num_sms;
-    k_split_gemm_tc<kSplitSlices><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(a, n_tiles);
+    k_split_gemm_tc<kSplitSlices><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(
+        a, n_tiles, *static_cast<const CUtensorMap*>(a.tmap));
   }
   else
     k_split_gemm<kSplitSlices><<<n_tiles, 256, mma_smem_bytes(kSplitSlices), s>>>(a);

@@ -24,6 +24,9 @@ struct SplitTable {
   void* A = nullptr;
   int* ea = nullptr;
   int M = 0, K = 0, Kpad = 0, nmat = 0;
+  // TMA tensor map (CUtensorMap) over the slices, viewed as [K/8 chunks][rows][8 elements] so that a
+  // box lands in shared memory as 8-row x 16-byte core matrices (tcgen05 engine)
+  alignas(128) unsigned char tmap[128] = {};
 };
 
 // m2m_lo / m2m_hi: the multipole-to-multipole operator split by children (0-1 and 2-3) so that
@@ -43,6 +46,7 @@ struct SplitArgs {
   const long long* a_mat;       // per group: matrix index
   const long long* src_vec;     // per column: vector index
   const long long* dst_off;     // per column: destination offset (elements of 8 bytes)
+  const void* tmap;             // host copy of the operator table's tensor map (tcgen05 engine)
 };
 
 struct DFReduceArgs {
