@@ -91,12 +91,13 @@ enum {
  *             sizes because K0(alpha r) is not scale invariant.
  *  order      expansion order P, 4 <= P <= 60 (40 gives about 12 digits, as in
  *             Sec. 3.2.1).
- *  precision  VP_PREC_FP64 (all contractions in FP64) or VP_PREC_SPLIT (the
- *             near-table, source-to-multipole, multipole-to-local,
- *             source-to-local, local-to-target and multipole-to-target
- *             contractions on the tensor cores from exact 8-bit slices of the
- *             FP64 operands, accumulated in double-float; multipole-to-
- *             multipole and local-to-local stay in FP64).
+ *  precision  VP_PREC_FP64 (all contractions in FP64) or VP_PREC_SPLIT (every
+ *             contraction -- near tables, source-to-multipole, multipole-to-
+ *             multipole, multipole-to-local, source-to-local, local-to-local,
+ *             local-to-target, multipole-to-target -- on the tensor cores from
+ *             exact 8-bit bf16 slices of the FP64 operands, folded in
+ *             double-float; the kernel values and the level scaling of the
+ *             operators are computed in FP64).
  *  stream     stream for the build kernels; the call synchronises it before
  *             returning.
  *  out        receives the handle; free with vp_tables_free.
@@ -234,9 +235,10 @@ int vp_eval_static(vp_tree tree, const double* f, double* u, double* gradu, void
 
 /*
  * Engines of the split-precision contractions (trees on VP_PREC_SPLIT tables):
- *  0  warp-level mma.sync m16n8k16 (fp16 in, fp32 accumulate in registers);
- *  1  tcgen05.mma kind::f16 issued by one thread per CTA, six fp32 accumulators in tensor memory,
- *     operands staged in shared memory; bounded mbarrier waits.
+ *  0  warp-level mma.sync m16n8k16 (bf16 slices in, four fp32 accumulators in registers);
+ *  1  tcgen05.mma kind::f16 (bf16 slices) issued by one thread of a persistent CTA per SM, four fp32
+ *     accumulators in tensor memory; operator slices staged by TMA, gathered source columns by
+ *     cp.async, a 4-stage ring handed over through mbarriers; every wait bounded.
  * Both compute the same exact slice sums. vp_tree_set_engine sets one engine for every launch of
  * the tree (VP_ERR_ARG for other values). vp_autotune times each split-precision launch of one
  * evaluation of `f` with both engines on `stream`, keeps the faster per launch, evaluates once more
