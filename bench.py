@@ -77,6 +77,29 @@ def dist_info():
     return rank, world, local
 
 
+def job_totals(units, total_ms, world, device):
+    """Whole-job totals over the ranks: units summed, timed milliseconds maxed (value = units / max)."""
+    if world <= 1:
+        return float(units), float(total_ms)
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    m = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(m, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(m.item())
+
+
+def barrier(world):
+    """Barrier over the ranks (if any) and a device synchronise."""
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -217,7 +240,7 @@ def choose_engine(V, args, tree, f, u, g):
     return V.vp_autotune(tree, f, u, g)
 
 
-def batched_form(args, V, ws, prec, local):
+def batched_form(args, V, ws, prec, local, world=1):
     """One form (FP64 or split) of the batched workload: graph replay timed per step, L2 flushed."""
     import torch
     t0 = time.perf_counter()
@@ -240,19 +263,22 @@ def batched_form(args, V, ws, prec, local):
         def timed(fn):
             for _ in range(args.warmup):
                 fn()
-            torch.cuda.synchronize()
+            barrier(world)
             total = 0.0
             for _ in range(args.steps):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream); fn(); e1.record(stream); e1.synchronize()
                 total += e0.elapsed_time(e1)
+            barrier(world)
             return total
 
         sampler = ClockSampler(local)
         with sampler:
             graph_ms = timed(lambda: V.vp_batch_run(batch))
         serial_ms = timed(lambda: V.vp_eval_batched(trees, fs, us, gs, use_graph=0))
+        nodes_all, graph_ms = job_totals(nodes, graph_ms, world, "cuda")
+        _, serial_ms = job_totals(nodes, serial_ms, world, "cuda")
         # dominant kernel: the near-field contraction of the largest tree, timed with events
         big = max(range(len(ws)), key=lambda k: ws[k].n_nodes)
         ms = [V.vp_eval_timed(vps[big].tree, fs[big], us[big], gs[big]) for _ in range(3)]
@@ -267,7 +293,8 @@ def batched_form(args, V, ws, prec, local):
             peak = measured_peaks().get("bf16_tflops", 1900.0)
             roof = {"kernel": "split-precision near GEMM, engine per launch (largest tree)", "bound": "tensor",
                     "peak_source": "measured dense bf16 burst, of measured"}
-        return {"nodes": int(nodes), "launches": int(launches), "graph_ms": graph_ms, "serial_ms": serial_ms,
+        return {"nodes": int(nodes), "nodes_all": nodes_all, "launches": int(launches), "graph_ms": graph_ms,
+                "serial_ms": serial_ms,
                 "setup_s": setup_s, "n_tc": n_tc, "clocks": sampler.summary(),
                 "roofline": dict(roof, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                                  traffic=None)}
@@ -285,14 +312,18 @@ def run_batched(args):
     from paper_1908_07392_gb300 import inputs as I
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     B.build()
+    # whole trees are sharded over the ranks (a different seeded batch per rank), no collective
     ws = I.batched_workloads(seed=4 + rank)
     head_prec = V.VP_PREC_FP64 if args.precision == "fp64" else V.VP_PREC_SPLIT
-    head = batched_form(args, V, ws, head_prec, local)
-    plain = batched_form(args, V, ws, V.VP_PREC_FP64, local) if args.precision == "both" else None
+    head = batched_form(args, V, ws, head_prec, local, world)
+    plain = batched_form(args, V, ws, V.VP_PREC_FP64, local, world) if args.precision == "both" else None
     split = head_prec == V.VP_PREC_SPLIT
     line = {"metric": "volume-potential leaf-nodes/s at stated rel err, split/batched vs plain FP64",
-            "value": head["nodes"] * args.steps / (head["graph_ms"] / 1000.0), "unit": "nodes/s", "n_gpus": world,
+            "value": head["nodes_all"] * args.steps / (head["graph_ms"] / 1000.0), "unit": "nodes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["graph_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+bf16-slices" if split else "f64", "data": "synthetic",
@@ -308,12 +339,15 @@ def run_batched(args):
             "roofline": head["roofline"], "cpu_baseline": None, "e2e": None,
             "gpu_launches": head["launches"] * args.steps, "clocks": head["clocks"]}
     if plain is not None:
-        pv = plain["nodes"] * args.steps / (plain["graph_ms"] / 1000.0)
+        pv = plain["nodes_all"] * args.steps / (plain["graph_ms"] / 1000.0)
         line["plain_fp64"] = {"value": pv, "unit": "nodes/s", "ms_per_step": plain["graph_ms"] / args.steps,
                               "roofline": plain["roofline"]}
         line["split_speedup_vs_fp64"] = line["value"] / pv
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def run_steps(args):
@@ -402,15 +436,9 @@ def measure(args, V, w, prec, world, local, with_e2e):
             V.vp_eval(vp.tree, f, u, g)
         torch.cuda.synchronize()
 
-        def barrier():
-            if world > 1:
-                import torch.distributed as dist
-                dist.barrier()
-            torch.cuda.synchronize()
-
         stage_ms, step_ms = [], []
         sampler = ClockSampler(local)
-        barrier()
+        barrier(world)
         with sampler:
             for _ in range(args.steps):
                 flush.zero_()
@@ -422,14 +450,9 @@ def measure(args, V, w, prec, world, local, with_e2e):
                 e1.synchronize()
                 step_ms.append(e0.elapsed_time(e1))
                 stage_ms.append(ms)
-        barrier()
-        total_ms = sum(step_ms)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
-        value = world * N * args.steps / (total_ms / 1000.0)
+        barrier(world)
+        units, total_ms = job_totals(N * args.steps, sum(step_ms), world, "cuda")
+        value = units / (total_ms / 1000.0)
 
         # e2e: host buffers, copies inside the timed region
         e2e = None
@@ -439,7 +462,7 @@ def measure(args, V, w, prec, world, local, with_e2e):
             gh = torch.empty(2, N, dtype=torch.float64).pin_memory()
             V.vp_eval_host(vp.tree, fh, uh, gh)
             torch.cuda.synchronize()
-            barrier()
+            barrier(world)
             t0 = time.perf_counter()
             for _ in range(args.steps):
                 V.vp_eval_host(vp.tree, fh, uh, gh)
