@@ -134,11 +134,36 @@ struct ReduceArgs {
 };
 
 __global__ void k_reduce(ReduceArgs a) {
+  constexpr int kChunk = 64;  // slot offsets staged in shared memory per pass
+  __shared__ long long slot_sh[kChunk];
   const int d = blockIdx.x;
   const long long b = a.ptr[d], e = a.ptr[d + 1];
-  for (int r = threadIdx.x; r < a.M; r += blockDim.x) {
-    double s = 0.0;
-    for (long long k = b; k < e; ++k) s += a.S[a.slot[k] + r];
+  const int rows_per_pass = (a.M + blockDim.x - 1) / blockDim.x;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // rows threadIdx.x + q blockDim.x, summed in slot order
+  for (long long c0 = b; c0 < e; c0 += kChunk) {
+    const int nc = (int)((e - c0) < kChunk ? (e - c0) : kChunk);
+    __syncthreads();
+    if (threadIdx.x < nc) slot_sh[threadIdx.x] = a.slot[c0 + threadIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= rows_per_pass) break;
+      const int r = threadIdx.x + q * blockDim.x;
+      if (r >= a.M) break;
+      int k = 0;
+      for (; k + 4 <= nc; k += 4) {
+        const double v0 = a.S[slot_sh[k] + r], v1 = a.S[slot_sh[k + 1] + r];
+        const double v2 = a.S[slot_sh[k + 2] + r], v3 = a.S[slot_sh[k + 3] + r];
+        acc[q] += v0; acc[q] += v1; acc[q] += v2; acc[q] += v3;
+      }
+      for (; k < nc; ++k) acc[q] += a.S[slot_sh[k] + r];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = threadIdx.x + q * blockDim.x;
+    if (q >= rows_per_pass || r >= a.M) break;
+    const double s = acc[q];
     if (a.final_out) {
       const int f = r / a.n, t = r - f * a.n;
       const long long o = a.dst_off[d] + t;  // leaf * n + t
@@ -704,6 +729,7 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
       a.S = bufs_c[d.src];
       if (a.final_out) { a.u = u; a.g = g; } else { a.Y = bufs[d.dst]; }
       const int threads = a.M >= 256 ? 256 : ((a.M + 31) / 32) * 32;
+      if (a.M > 4 * threads) return VP_ERR_ARG;  // at most 4 rows per thread (3 p^2 <= 768)
       k_reduce<<<d.n_dst, threads, 0, s>>>(a);
       TRY(cudaGetLastError());
     } else if (st.kind == 3) {
@@ -1240,6 +1266,7 @@ extern "C" int vp_eval_static(vp_tree tree, const double* f, double* u, double* 
       a.S = bufs_c[d.src];
       if (a.final_out) { a.u = u; a.g = gradu; } else { a.Y = bufs[d.dst]; }
       const int threads = a.M >= 256 ? 256 : ((a.M + 31) / 32) * 32;
+      if (a.M > 4 * threads) return VP_ERR_ARG;  // at most 4 rows per thread (3 p^2 <= 768)
       k_reduce<<<d.n_dst, threads, 0, s>>>(a);
       TRY(cudaGetLastError());
     } else {

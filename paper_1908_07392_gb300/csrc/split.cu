@@ -613,17 +613,45 @@ size_t tc_smem_bytes(int S) { return (size_t)kTcStages * S * (kTcA + kTcB) * siz
 
 // Reduction of double-float slots: y[dst] = sum of slots (double-float), written as FP64.
 __global__ void k_reduce_df(DFReduceArgs a) {
+  constexpr int kChunk = 64;  // slot offsets staged in shared memory per pass
+  __shared__ long long slot_sh[kChunk];
   const int d = blockIdx.x;
   const long long b = a.ptr[d], e = a.ptr[d + 1];
   const float2* S = reinterpret_cast<const float2*>(a.S);
-  for (int r = threadIdx.x; r < a.M; r += blockDim.x) {
-    float hi = 0.f, lo = 0.f;
-    for (long long k = b; k < e; ++k) {
-      const float2 v = S[a.slot[k] + r];
-      df_add(hi, lo, v.x);
-      df_add(hi, lo, v.y);
+  const int rows_per_pass = (a.M + blockDim.x - 1) / blockDim.x;
+  // each thread owns up to 4 rows (M <= 4 * blockDim.x), summed in slot order
+  float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+  for (long long c0 = b; c0 < e; c0 += kChunk) {
+    const int nc = (int)((e - c0) < kChunk ? (e - c0) : kChunk);
+    __syncthreads();
+    if (threadIdx.x < nc) slot_sh[threadIdx.x] = a.slot[c0 + threadIdx.x];
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= rows_per_pass) break;
+      const int r = threadIdx.x + q * blockDim.x;
+      if (r >= a.M) break;
+      int k = 0;
+      for (; k + 4 <= nc; k += 4) {  // four loads in flight, added in slot order
+        const float2 v0 = S[slot_sh[k] + r], v1 = S[slot_sh[k + 1] + r];
+        const float2 v2 = S[slot_sh[k + 2] + r], v3 = S[slot_sh[k + 3] + r];
+        df_add(hi[q], lo[q], v0.x); df_add(hi[q], lo[q], v0.y);
+        df_add(hi[q], lo[q], v1.x); df_add(hi[q], lo[q], v1.y);
+        df_add(hi[q], lo[q], v2.x); df_add(hi[q], lo[q], v2.y);
+        df_add(hi[q], lo[q], v3.x); df_add(hi[q], lo[q], v3.y);
+      }
+      for (; k < nc; ++k) {
+        const float2 v = S[slot_sh[k] + r];
+        df_add(hi[q], lo[q], v.x);
+        df_add(hi[q], lo[q], v.y);
+      }
     }
-    const double s = (double)hi + (double)lo;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = threadIdx.x + q * blockDim.x;
+    if (q >= rows_per_pass || r >= a.M) break;
+    const double s = (double)hi[q] + (double)lo[q];
     if (a.final_out) {
       const int f = r / a.n, t = r - f * a.n;
       const long long o = a.dst_off[d] + t;
@@ -777,6 +805,7 @@ int launch_slice_list(const double* X, const long long* base, const long long* v
 int launch_reduce_df(const DFReduceArgs& a, int n_dst, cudaStream_t s) {
   if (n_dst <= 0) return VP_OK;
   const int threads = a.M >= 256 ? 256 : ((a.M + 31) / 32) * 32;
+  if (a.M > 4 * threads) return VP_ERR_ARG;  // rows per thread are held in registers (3 p^2 <= 768)
   k_reduce_df<<<n_dst, threads, 0, s>>>(a);
   TRY(cudaGetLastError());
   return VP_OK;
