@@ -155,6 +155,10 @@ int vp_tree_interp(vp_tree tree, int n_fields, const double* fields, int n_point
  *  gradu  device [2][N] output: du/dx then du/dy.
  * Outputs are overwritten. The tree's work buffers are reused, so calls on
  * one tree must not overlap on the GPU (issue them on one stream).
+ * Inside one call the near-field contraction runs on `stream` while the
+ * far-field chain runs on a high-priority stream owned by the tree, forked
+ * from and joined back to `stream` with events, so the call stays ordered on
+ * `stream` as a whole (also under stream capture).
  * Errors: VP_ERR_ARG, VP_ERR_CUDA (launch failures are reported; asynchronous
  * faults surface at the next synchronising call).
  */
@@ -181,9 +185,10 @@ enum {
 };
 
 /*
- * vp_eval_timed -- vp_eval with a CUDA event recorded on `stream` between
- * stages; waits for the last event and writes the milliseconds of each stage
- * to stage_ms[VP_NSTAGES] (host array). Same arguments and errors as vp_eval.
+ * vp_eval_timed -- vp_eval with every stage issued in order on `stream` (no
+ * overlap) and a CUDA event recorded between stages; waits for the last event
+ * and writes the milliseconds of each stage to stage_ms[VP_NSTAGES] (host
+ * array). Same arguments and errors as vp_eval.
  */
 int vp_eval_timed(vp_tree tree, const double* f, double* u, double* gradu, void* stream, float* stage_ms);
 

@@ -329,6 +329,10 @@ struct vp_tree_s {
   double *d_f = nullptr, *d_u = nullptr, *d_g = nullptr;
   // point location for vp_tree_interp: finest-level cell -> leaf, built on first use
   int* d_cell = nullptr;
+  // overlap of the near field with the far-field chain (vp_eval): the chain runs on `side`, a
+  // high-priority stream, the near field on the caller's stream; events fork and join them
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_src = nullptr, ev_join = nullptr;
 };
 
 namespace vp {
@@ -703,15 +707,37 @@ SplitArgs split_args(const vp_tree_s* tr, const DevSplit& d, double* const* bufs
   return a;
 }
 
-int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+// Issue one evaluation. With per-stage events (ev) every step goes to `s` in order. Otherwise the
+// near-field steps, which need only the source (and its slices), run on `s` while the far-field
+// chain (upward, M2L, downward, targets) runs on the tree's high-priority side stream; near-field
+// CTAs then hold one tile each, so chain launches find SMs; `s` waits for the chain before the
+// output reduction. The two write disjoint contribution slots.
+int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t s0, cudaEvent_t* ev = nullptr) {
   const vp_tables_s* T = tr->T;
   int stage = -1;
   const double* bufs_c[BUF_COUNT] = {f, tr->mp, tr->loc, tr->lslot, tr->uslot};
   double* bufs[BUF_COUNT] = {nullptr, tr->mp, tr->loc, tr->lslot, tr->uslot};
+  const bool overlap = !ev && tr->side;
+  bool src_ready = false, near_started = false, joined = !overlap;
+  if (overlap) {
+    TRY(cudaEventRecord(tr->ev_fork, s0));
+    TRY(cudaStreamWaitEvent(tr->side, tr->ev_fork, 0));
+  }
   for (const Step& st : tr->steps) {
     if (ev) {
-      while (stage < st.stage) { ++stage; TRY(cudaEventRecord(ev[stage], s)); }
+      while (stage < st.stage) { ++stage; TRY(cudaEventRecord(ev[stage], s0)); }
     }
+    const bool near_step = overlap && st.stage == VP_STAGE_NEAR;
+    if (overlap && st.stage == VP_STAGE_OUTPUT && !joined) {
+      TRY(cudaEventRecord(tr->ev_join, tr->side));
+      TRY(cudaStreamWaitEvent(s0, tr->ev_join, 0));
+      joined = true;
+    }
+    if (near_step && !near_started) {
+      if (src_ready) TRY(cudaStreamWaitEvent(s0, tr->ev_src, 0));  // sliced source made on the chain
+      near_started = true;
+    }
+    const cudaStream_t s = (!overlap || near_step || st.stage == VP_STAGE_OUTPUT) ? s0 : tr->side;
     if (st.kind == 2) {
       TRY(cudaMemsetAsync(tr->mp, 0, (size_t)tr->n_boxes * T->E * sizeof(double), s));
     } else if (st.kind == 0) {
@@ -737,10 +763,14 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
       const int rc = launch_slice_list(bufs_c[d.buf], d.base, d.vid, d.n, d.K, d.kseg, d.seg_stride, d.cstride,
                                        tr->sv[d.family], tr->se[d.family], s);
       if (rc) return rc;
+      if (overlap && d.family == 0 && !near_started) {
+        TRY(cudaEventRecord(tr->ev_src, s));
+        src_ready = true;
+      }
     } else if (st.kind == 4) {
       const DevSplit& d = tr->splits[st.index];
       SplitArgs a = split_args(tr, d, bufs);
-      const int rc = launch_split_gemm(a, d.n_tiles[d.engine], s, d.engine);
+      const int rc = launch_split_gemm(a, d.n_tiles[d.engine], s, d.engine, near_step ? 1 : 0);
       if (rc) return rc;
     } else if (st.kind == 5) {
       const DevReduce& d = tr->reduces[st.index];
@@ -753,8 +783,12 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
       if (rc) return rc;
     }
   }
+  if (!joined) {
+    TRY(cudaEventRecord(tr->ev_join, tr->side));
+    TRY(cudaStreamWaitEvent(s0, tr->ev_join, 0));
+  }
   if (ev) {
-    while (stage < VP_NSTAGES) { ++stage; TRY(cudaEventRecord(ev[stage], s)); }
+    while (stage < VP_NSTAGES) { ++stage; TRY(cudaEventRecord(ev[stage], s0)); }
   }
   return VP_OK;
 }
@@ -791,6 +825,15 @@ extern "C" int vp_tree_upload(vp_tables tables, double cx, double cy, int n_leav
     if ((rc = dev_upload(tr.get(), xi, &tr->d_xi, s))) return fail(rc);
   }
   if ((rc = build_tree(tr.get(), P, s))) return fail(rc);
+  {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&tr->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&tr->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&tr->ev_src, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&tr->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(VP_ERR_CUDA);
+  }
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { set_last_cuda(e); return fail(VP_ERR_CUDA); }
   *out = tr.release();
@@ -901,6 +944,9 @@ extern "C" int vp_eval_host(vp_tree tree, const double* f, double* u, double* gr
 
 extern "C" void vp_tree_free(vp_tree tree) {
   if (!tree) return;
+  if (tree->side) cudaStreamDestroy(tree->side);
+  for (cudaEvent_t e : {tree->ev_fork, tree->ev_src, tree->ev_join})
+    if (e) cudaEventDestroy(e);
   for (void* p : tree->allocs) cudaFree(p);
   delete tree;
 }

@@ -774,7 +774,7 @@ int read_split_error(int* flag) {
   return VP_OK;
 }
 
-int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engine) {
+int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engine, int short_ctas) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   TRY(cudaStreamIsCapturing(s, &cs));
   if (cs == cudaStreamCaptureStatusNone) {
@@ -783,7 +783,7 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engin
   }
   if (n_tiles <= 0) return VP_OK;
   if (engine == kEngineTcgen05) {
-    const int grid = n_tiles < g_num_sms ? n_tiles : g_num_sms;
+    const int grid = (short_ctas || n_tiles < g_num_sms) ? n_tiles : g_num_sms;
     k_split_gemm_tc<kSplitSlices><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(
         a, n_tiles, *static_cast<const CUtensorMap*>(a.tmap));
   }

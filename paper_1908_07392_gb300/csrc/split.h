@@ -69,7 +69,9 @@ constexpr int kSplitBN[2] = {64, 128};           // columns per tile, by engine
 int build_split(vp_tables_s* T, cudaStream_t s);
 void free_split_tables(vp_tables_s* T);
 int prepare_split_launch();
-int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engine);
+// short_ctas: tcgen05 CTAs take one tile each (so other kernels can interleave) instead of one
+// persistent CTA per SM.
+int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engine, int short_ctas = 0);
 // Read and clear the flag that a bounded wait of the tcgen05 engine gave up.
 int read_split_error(int* flag);
 int launch_slice_list(const double* X, const long long* base, const long long* vid, long long nlist, int K, int kseg,
