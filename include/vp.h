@@ -166,10 +166,12 @@ int vp_eval(vp_tree tree, const double* f, double* u, double* gradu, void* strea
 
 /*
  * vp_eval_host -- vp_eval from and to HOST memory.
- *  f (host [N]) is copied to the device, the potential is evaluated, and u
- *  (host [N]) and gradu (host [2][N]) are copied back; the call synchronises
- *  `stream` before returning. Pinned host memory makes the copies faster.
- *  Device staging buffers are owned by the tree (allocated on first use).
+ *  f (host [N]) in, u (host [N]) and gradu (host [2][N]) out; the call
+ *  synchronises `stream` before returning. Page-locked buffers (cudaHostAlloc,
+ *  cudaHostRegister) are used in place: the output reduction writes u and
+ *  gradu straight into them, and trees on VP_PREC_SPLIT tables read f from
+ *  them (f is read once, by the slicing kernel). Other buffers go through
+ *  device staging copies owned by the tree (allocated on first use).
  */
 int vp_eval_host(vp_tree tree, const double* f, double* u, double* gradu, void* stream);
 

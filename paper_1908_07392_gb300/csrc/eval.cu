@@ -922,22 +922,49 @@ extern "C" int vp_tree_stats(vp_tree tree, int64_t* launches, double* stage_flop
   return VP_OK;
 }
 
+namespace {
+// Device address of page-locked host memory (cudaHostAlloc / cudaHostRegister), or null for any
+// other pointer.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+}  // namespace
+
 extern "C" int vp_eval_host(vp_tree tree, const double* f, double* u, double* gradu, void* stream) {
   if (!tree || !f || !u || !gradu) return VP_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t N = (size_t)tree->N;
-  if (!tree->d_f) {
+  // Page-locked host buffers are used in place: the output reduction writes u and grad u straight
+  // into them, and in the split form (where only the slicing kernel reads f) f is read from the
+  // host as well. Other buffers go through device copies.
+  const void* fm = tree->T->precision == VP_PREC_SPLIT ? mapped_host(f) : nullptr;
+  void* um = const_cast<void*>(mapped_host(u));
+  void* gm = const_cast<void*>(mapped_host(gradu));
+  if (!tree->d_f && (!fm || !um || !gm)) {
     TRY(cudaMalloc(&tree->d_f, N * sizeof(double)));
     tree->allocs.push_back(tree->d_f);
     TRY(cudaMalloc(&tree->d_u, 3 * N * sizeof(double)));
     tree->allocs.push_back(tree->d_u);
     tree->d_g = tree->d_u + N;
   }
-  TRY(cudaMemcpyAsync(tree->d_f, f, N * sizeof(double), cudaMemcpyHostToDevice, s));
-  const int rc = run_steps(tree, tree->d_f, tree->d_u, tree->d_g, s);
+  const double* fd = static_cast<const double*>(fm);
+  if (!fd) {
+    TRY(cudaMemcpyAsync(tree->d_f, f, N * sizeof(double), cudaMemcpyHostToDevice, s));
+    fd = tree->d_f;
+  }
+  double* ud = um && gm ? static_cast<double*>(um) : tree->d_u;
+  double* gd = um && gm ? static_cast<double*>(gm) : tree->d_g;
+  const int rc = run_steps(tree, fd, ud, gd, s);
   if (rc) return rc;
-  TRY(cudaMemcpyAsync(u, tree->d_u, N * sizeof(double), cudaMemcpyDeviceToHost, s));
-  TRY(cudaMemcpyAsync(gradu, tree->d_g, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (ud == tree->d_u) {
+    TRY(cudaMemcpyAsync(u, tree->d_u, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TRY(cudaMemcpyAsync(gradu, tree->d_g, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, s));
+  }
   TRY(cudaStreamSynchronize(s));
   return VP_OK;
 }

@@ -74,3 +74,26 @@ def test_split_rejected_by_the_static_entry_point():
         assert rc == -1
     finally:
         vp.close()
+
+
+@pytest.mark.parametrize("precision", [V.VP_PREC_FP64, V.VP_PREC_SPLIT])
+def test_host_entry_point_with_pinned_and_pageable_buffers(precision):
+    # page-locked buffers are used in place (outputs written by the reduction, split-form input read
+    # by the slicing kernel); pageable ones go through staging copies; both give the device path's bits
+    import torch
+    w = I.small_gaussian_workload()
+    vp = V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, precision=precision)
+    try:
+        f = torch.from_numpy(np.ascontiguousarray(w.f))
+        u_dev, g_dev = vp(f.cuda())
+        torch.cuda.synchronize()
+        fp = f.pin_memory()
+        up = torch.zeros(w.n_nodes, dtype=torch.float64).pin_memory()
+        gp = torch.zeros(2, w.n_nodes, dtype=torch.float64).pin_memory()
+        V.vp_eval_host(vp.tree, fp, up, gp)
+        assert torch.equal(up, u_dev.cpu()) and torch.equal(gp, g_dev.cpu())
+        un = np.zeros(w.n_nodes); gn = np.zeros((2, w.n_nodes))
+        V.vp_eval_host(vp.tree, f.numpy(), un, gn)
+        assert np.array_equal(un, u_dev.cpu().numpy()) and np.array_equal(gn, g_dev.cpu().numpy())
+    finally:
+        vp.close()
