@@ -362,6 +362,31 @@ __device__ inline void mbar_arrive(unsigned long long* bar) {
   asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// One tcgen05.mma kind::f16 (A and B from shared-memory descriptors) with an A-collector usage:
+// U = 0 none, 1 fill, 2 use, 3 lastuse.
+template <int U>
+__device__ inline void umma_f16(unsigned d_tmem, unsigned long long da, unsigned long long db, unsigned idesc,
+                                unsigned accum) {
+  if constexpr (U == 0) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                 "l"(da), "l"(db), "r"(idesc), "r"(accum));
+  } else if constexpr (U == 1) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                 "l"(da), "l"(db), "r"(idesc), "r"(accum));
+  } else if constexpr (U == 2) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                 "l"(da), "l"(db), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                     d_tmem),
+                 "l"(da), "l"(db), "r"(idesc), "r"(accum));
+  }
+}
+
 __device__ inline void umma_commit(unsigned long long* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
                : "memory");
@@ -581,10 +606,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const unsigned d_tmem = tmem + (unsigned)(w * kTcN);
             // the first product of each accumulator in a tile (step 0, i = 0, j = w) overwrites it
             const unsigned accum = (k == 0 && i == 0 && j == w) ? 0u : 1u;
-            asm volatile(
-                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-                "l"(da), "l"(db), "r"(idesc), "r"(accum));
+            // A slice i serves the S - i products j = 0 .. S-1-i: it is read from shared memory once
+            // into the A collector buffer and reused by the following MMAs
+            const int uses = S - i;
+            if (uses == 1) umma_f16<0>(d_tmem, da, db, idesc, accum);
+            else if (j == 0) umma_f16<1>(d_tmem, da, db, idesc, accum);
+            else if (j < uses - 1) umma_f16<2>(d_tmem, da, db, idesc, accum);
+            else umma_f16<3>(d_tmem, da, db, idesc, accum);
           }
         }
         umma_commit(&empty[st]);

@@ -75,3 +75,38 @@ def test_autotune_keeps_results_and_uses_the_cache(tmp_path):
         assert open(cache).read().strip().splitlines() == lines
     finally:
         vp.close()
+
+
+@pytest.mark.parametrize("depth,p", [(0, 6), (1, 8), (2, 16)])
+def test_tcgen05_shallow_trees_against_oracle(depth, p):
+    # a root leaf (one near tile, no far field), 4 leaves, 16 leaves: ragged and single-tile launches
+    w = I.small_gaussian_workload(depth=depth, p=p)
+    (u0, g0), (u1, g1) = _both_engines(w)
+    assert rel_err(u1, u0) < 1e-13 and rel_err(g1, g0) < 1e-13
+    ou, oux, ouy = oracle_eval(w)
+    errs = (rel_err(u1, ou), rel_err(g1[0], oux), rel_err(g1[1], ouy))
+    assert max(errs) < TOL_SPLIT, errs
+
+
+@pytest.mark.parametrize("precision", [V.VP_PREC_FP64, V.VP_PREC_SPLIT])
+def test_overlapped_and_in_order_evaluations_agree_bitwise(precision):
+    # vp_eval runs the near field beside the far-field chain; vp_eval_timed runs the stages in order:
+    # the arithmetic per output is the same, so the bits are
+    import torch
+    rng = np.random.default_rng(31)
+    tree = I.random_balanced_tree(rng, 30, 6, side=3.0, min_depth=2)
+    X, Y = I.node_coords(tree, 8)
+    fn = I.gaussian_sum(rng.uniform(-0.8, 0.8, (3, 2)), rng.uniform(0.1, 0.4, 3), rng.uniform(-1, 1, 3))
+    vp = V.VolumePotential(1, 100.0, 8, tree, precision=precision)
+    try:
+        f = torch.from_numpy(fn(X, Y)).cuda()
+        u1, g1 = vp(f)
+        u2 = torch.empty_like(u1); g2 = torch.empty_like(g1)
+        V.vp_eval_timed(vp.tree, f, u2, g2)
+        torch.cuda.synchronize()
+        assert torch.equal(u1, u2) and torch.equal(g1, g2)
+        for _ in range(3):
+            u3, g3 = vp(f)
+            assert torch.equal(u3, u1) and torch.equal(g3, g1)
+    finally:
+        vp.close()
