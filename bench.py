@@ -405,6 +405,9 @@ def run_steps(args):
             "held_out": ev,
             "iterations_saved_vs_cold": ev["cold"]["mean_iters"] - ev["network"]["mean_iters"],
             "iterations_saved_vs_extrapolation": ev["extrapolation"]["mean_iters"] - ev["network"]["mean_iters"],
+            "augmented_iterations_saved_vs_cold": ev["cold"]["mean_iters"] - ev["network_aug"]["mean_iters"],
+            "augmented_iterations_saved_vs_extrapolation":
+                ev["extrapolation"]["mean_iters"] - ev["network_aug"]["mean_iters"],
             "plain_mean_iters": r["plain_mean_iters"], "volume_ms_mean": r["volume_ms_mean"],
             "train_seconds": r["train_seconds"], "train_loss": [r["first_train_loss"], r["final_train_loss"]],
             "interior_rel_err_exact_solution": err, "wall_seconds": wall,

@@ -54,6 +54,19 @@ int bie_apply(bie b, const double* mu, double* out, void* stream);
  */
 int bie_solve(bie b, const double* g, double* mu, double tol, int max_iter, int* iters, double* relres, void* stream);
 
+/*
+ * bie_solve_aug -- bie_solve with one augmentation direction d (device [2N], 16-byte aligned, or
+ * NULL for plain bie_solve), e.g. a predicted correction to the initial guess. First the
+ * least-squares step along d is taken (mu += s d with s minimising |r - s A d|); then GMRES runs on
+ * the operator projected off c = A d / |A d| (each new Krylov vector loses its c component, whose
+ * coefficients b_j are kept), and the final update is mu += V y - (b . y) d / |A d|. The residual
+ * estimate of the projected Hessenberg system is the true residual, so the iteration stops at the
+ * same tolerance, and the d direction stays resolved throughout. Same arguments and errors as
+ * bie_solve otherwise.
+ */
+int bie_solve_aug(bie b, const double* g, double* mu, const double* d, double tol, int max_iter, int* iters,
+                  double* relres, void* stream);
+
 /* u = D[mu] at n_targets interior points txy [2][M] (plain quadrature: keep targets a few panel
  * lengths away from the boundary); u device [2][M]. */
 int bie_eval(bie b, const double* mu, int n_targets, const double* txy, double* u, void* stream);

@@ -69,6 +69,8 @@ def load_library():
     lib.bie_apply.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     lib.bie_solve.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, ctypes.POINTER(c_int),
                               ctypes.POINTER(c_double), c_void_p]
+    lib.bie_solve_aug.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, ctypes.POINTER(c_int),
+                                  ctypes.POINTER(c_double), c_void_p]
     lib.bie_eval.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     lib.bie_stokeslets.argtypes = [c_double, c_int, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
     lib.bie_kernel_scalars.argtypes = [c_int, c_void_p, c_void_p, c_void_p]
@@ -107,7 +109,7 @@ def exported_symbols():
             "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
             "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status",
-            "bie_create", "bie_free", "bie_size", "bie_nodes", "bie_apply", "bie_solve", "bie_eval",
+            "bie_create", "bie_free", "bie_size", "bie_nodes", "bie_apply", "bie_solve", "bie_solve_aug", "bie_eval",
             "bie_stokeslets", "bie_kernel_scalars", "ws_create", "ws_free", "ws_num_params", "ws_params",
             "ws_forward", "ws_grad", "ws_train_step"]
 
@@ -383,14 +385,17 @@ class BIE:
         _check(load_library().bie_apply(ctypes.c_void_p(self.handle), _p(mu), _p(out), _stream_ptr(stream)), "bie_apply")
         return out
 
-    def solve(self, g, mu0=None, tol=1e-11, max_iter=None, stream=None):
-        """Returns (mu, iterations, true relative residual); mu0 is the initial guess (zeros if None)."""
+    def solve(self, g, mu0=None, tol=1e-11, max_iter=None, stream=None, aug=None):
+        """Returns (mu, iterations, true relative residual); mu0 is the initial guess (zeros if None);
+        aug an optional augmentation direction (bie_solve_aug)."""
         import torch
         mu = torch.zeros_like(g) if mu0 is None else mu0.clone()
         it = ctypes.c_int(); rr = ctypes.c_double()
-        _check(load_library().bie_solve(ctypes.c_void_p(self.handle), _p(g), _p(mu), float(tol),
-                                        int(max_iter or self.max_krylov), ctypes.byref(it), ctypes.byref(rr),
-                                        _stream_ptr(stream)), "bie_solve")
+        augc = aug.contiguous() if aug is not None else None
+        d = ctypes.c_void_p(augc.data_ptr()) if augc is not None else ctypes.c_void_p(0)
+        _check(load_library().bie_solve_aug(ctypes.c_void_p(self.handle), _p(g), _p(mu), d, float(tol),
+                                            int(max_iter or self.max_krylov), ctypes.byref(it), ctypes.byref(rr),
+                                            _stream_ptr(stream)), "bie_solve_aug")
         return mu, it.value, rr.value
 
     def eval(self, mu, txy, stream=None):

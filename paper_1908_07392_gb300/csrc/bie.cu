@@ -387,6 +387,42 @@ __global__ void k_gm_step(int j, int m, double tol, GmresCtl* ctl, double* H, do
   if (ctl->res <= tol || hn == 0.0) ctl->done = 1;
 }
 
+// Augmentation by a direction d (w = A d on entry): with s = (w.r)/(w.w), mu += s d, r -= s w
+// (the least-squares step along d), c = w/|w|, u = d/|w|; nothing when w = 0.
+__global__ void k_aug_setup(int n, const double* ww_wr, const double* w, const double* d, double* r, double* mu,
+                            double* c, double* u) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double ww = ww_wr[0], wr = ww_wr[1];
+  if (!(ww > 0.0)) {
+    c[k] = 0.0;
+    u[k] = 0.0;
+    return;
+  }
+  const double nrm = sqrt(ww), st = wr / ww;
+  mu[k] += st * d[k];
+  r[k] -= st * w[k];
+  c[k] = w[k] / nrm;
+  u[k] = d[k] / nrm;
+}
+
+// w -= beta c, beta = *bj (the component of A v_j along c, removed from the Krylov operator).
+__global__ void k_aug_project(int n, const GmresCtl* ctl, const double* bj, const double* c, double* w) {
+  if (gm_done(ctl)) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) w[k] -= *bj * c[k];
+}
+
+// mu -= (sum_{j < it} b_j y_j) u: the update V y moved A mu by the removed components c b.y.
+__global__ void k_aug_final(int n, const GmresCtl* ctl, const double* bv, const double* y, const double* u,
+                            double* mu) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double sdot = 0.0;
+  for (int j = 0; j < ctl->it; ++j) sdot += bv[j] * y[j];
+  mu[k] -= sdot * u[k];
+}
+
 // Least-squares solution of the rotated Hessenberg system (one thread, back substitution).
 __global__ void k_gm_backsub(int m, const GmresCtl* ctl, const double* H, const double* gv, double* y) {
   const int it = ctl->it;
@@ -464,6 +500,7 @@ struct bie_s {
   int m = 0;
   double *V = nullptr, *w = nullptr, *r = nullptr;
   double* gm = nullptr;          // H [(m+1) m], cs [m], sn [m], gv [m+2], y [m], hv [2(m+1)], scalars [8]
+  double *ac = nullptr, *au = nullptr, *abv = nullptr;  // augmentation: c, u [2N], b [m]
   vp::GmresCtl* ctl = nullptr;   // device
   vp::GmresCtl* hctl = nullptr;  // pinned host copy
 };
@@ -525,7 +562,8 @@ extern "C" int bie_create(double alpha, double R, double A, int k, double phase,
   if ((rc = dalloc(B.get(), &B->V, (size_t)(B->m + 1) * B->n2)) || (rc = dalloc(B.get(), &B->w, B->n2)) ||
       (rc = dalloc(B.get(), &B->r, B->n2)) ||
       (rc = dalloc(B.get(), &B->gm, (size_t)(B->m + 1) * B->m + 6 * (size_t)B->m + 12)) ||
-      (rc = dalloc(B.get(), &B->ctl, 1))) {
+      (rc = dalloc(B.get(), &B->ctl, 1)) || (rc = dalloc(B.get(), &B->ac, B->n2)) ||
+      (rc = dalloc(B.get(), &B->au, B->n2)) || (rc = dalloc(B.get(), &B->abv, B->m))) {
     bie_free(B.release());
     return rc;
   }
@@ -581,9 +619,11 @@ extern "C" int bie_apply(bie b, const double* mu, double* out, void* stream) {
   return VP_OK;
 }
 
-extern "C" int bie_solve(bie b, const double* g, double* mu, double tol, int max_iter, int* iters, double* relres,
-                         void* stream) {
-  if (!b || !g || !mu || !(tol > 0.0) || max_iter < 1 || (reinterpret_cast<uintptr_t>(mu) & 15)) return VP_ERR_ARG;
+extern "C" int bie_solve_aug(bie b, const double* g, double* mu, const double* d, double tol, int max_iter,
+                             int* iters, double* relres, void* stream) {
+  if (!b || !g || !mu || !(tol > 0.0) || max_iter < 1 || (reinterpret_cast<uintptr_t>(mu) & 15) ||
+      (reinterpret_cast<uintptr_t>(d) & 15))
+    return VP_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = b->n2, M = b->m;
   const int m = std::min(max_iter, M);
@@ -599,6 +639,13 @@ extern "C" int bie_solve(bie b, const double* g, double* mu, double tol, int max
   // r = g - A mu, norms, V0 = r / |r|
   k_gemv<<<GV, 256, 0, s>>>(n, b->A, mu, b->r);
   k_axpby<<<G, T, 0, s>>>(n, 1.0, g, -1.0, b->r);
+  if (d) {
+    // least-squares step along d, then GMRES on (I - c c^T) A so that direction stays removed
+    k_gemv<<<GV, 256, 0, s>>>(n, b->A, d, b->w);
+    k_dots<<<1, 256, 0, s>>>(n, 1, b->w, b->w, wn2 + 4);
+    k_dots<<<1, 256, 0, s>>>(n, 1, b->w, b->r, wn2 + 5);
+    k_aug_setup<<<G, T, 0, s>>>(n, wn2 + 4, b->w, d, b->r, mu, b->ac, b->au);
+  }
   k_dots<<<1, 256, 0, s>>>(n, 1, g, g, wn2);
   k_dots<<<1, 256, 0, s>>>(n, 1, b->r, b->r, wn2 + 1);
   k_gm_init<<<1, 1, 0, s>>>(ctl, wn2, tol, gv);
@@ -611,6 +658,10 @@ extern "C" int bie_solve(bie b, const double* g, double* mu, double tol, int max
     for (; j < jend; ++j) {
       const double* vj = b->V + (size_t)j * n;
       k_gemv<<<GV, 256, 0, s>>>(n, b->A, vj, b->w, ctl);
+      if (d) {
+        k_dots<<<1, 256, 0, s>>>(n, 1, b->ac, b->w, b->abv + j, ctl);
+        k_aug_project<<<G, T, 0, s>>>(n, ctl, b->abv + j, b->ac, b->w);
+      }
       for (int pass = 0; pass < 2; ++pass) {
         k_dots<<<j + 1, 256, 0, s>>>(n, j + 1, b->V, b->w, hv + pass * (M + 1), ctl);
         k_sub_proj<<<G, T, 0, s>>>(n, j + 1, b->V, hv + pass * (M + 1), b->w, ctl);
@@ -626,6 +677,7 @@ extern "C" int bie_solve(bie b, const double* g, double* mu, double tol, int max
   // update and the true residual
   k_gm_backsub<<<1, 1, 0, s>>>(M, ctl, H, gv, y);
   k_add_comb<<<G, T, 0, s>>>(n, ctl, b->V, y, mu);
+  if (d) k_aug_final<<<G, T, 0, s>>>(n, ctl, b->abv, y, b->au, mu);
   k_gemv<<<GV, 256, 0, s>>>(n, b->A, mu, b->r);
   k_axpby<<<G, T, 0, s>>>(n, 1.0, g, -1.0, b->r);
   k_dots<<<1, 256, 0, s>>>(n, 1, b->r, b->r, wn2 + 3);
@@ -637,6 +689,11 @@ extern "C" int bie_solve(bie b, const double* g, double* mu, double tol, int max
   if (relres) *relres = std::sqrt(std::max(rr[0], 0.0)) / b->hctl->bnorm;
   TRY(cudaGetLastError());
   return VP_OK;
+}
+
+extern "C" int bie_solve(bie b, const double* g, double* mu, double tol, int max_iter, int* iters, double* relres,
+                         void* stream) {
+  return bie_solve_aug(b, g, mu, nullptr, tol, max_iter, iters, relres, stream);
 }
 
 extern "C" int bie_eval(bie b, const double* mu, int n_targets, const double* txy, double* u, void* stream) {

@@ -111,3 +111,26 @@ def test_warm_start_reduces_gmres_iterations():
     assert ev["network"]["mean_iters"] < ev["cold"]["mean_iters"]
     assert ev["extrapolation"]["mean_iters"] < ev["cold"]["mean_iters"]
     assert r["final_train_loss"] < r["first_train_loss"]
+
+
+def test_augmented_gmres():
+    # one augmentation direction: the exact correction solves the system in the least-squares step;
+    # an arbitrary direction still converges to the same density; a zero direction is plain GMRES
+    import torch
+    b = V.BIE(30.0, R=1.0, A=0.3, k=5, phase=0.2, n_panels=32)
+    try:
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        g = torch.randn(2 * b.N, dtype=torch.float64, device="cuda", generator=gen)
+        ref, it0, rr0 = b.solve(g, None, 1e-13)
+        x0 = 0.9 * ref + 1e-3 * torch.randn(2 * b.N, dtype=torch.float64, device="cuda", generator=gen)
+        mu, it, rr = b.solve(g, x0, 1e-13, aug=ref - x0)
+        assert rr < 1e-12 and it <= 1
+        assert float((mu - ref).abs().max()) < 1e-10 * float(ref.abs().max())
+        d = torch.randn(2 * b.N, dtype=torch.float64, device="cuda", generator=gen)
+        mu2, it2, rr2 = b.solve(g, x0, 1e-13, aug=d)
+        assert rr2 < 1e-12 and float((mu2 - ref).abs().max()) < 1e-10 * float(ref.abs().max())
+        mu3, it3, rr3 = b.solve(g, x0, 1e-13, aug=torch.zeros_like(d))
+        mu4, it4, rr4 = b.solve(g, x0, 1e-13)
+        assert it3 == it4 and torch.equal(mu3, mu4)
+    finally:
+        b.close()
