@@ -30,12 +30,16 @@ def _workloads():
     return ws
 
 
-@pytest.mark.parametrize("precision", [V.VP_PREC_FP64, V.VP_PREC_SPLIT])
-def test_batch_graph_matches_single_tree_evaluations(precision):
+@pytest.mark.parametrize("precision,engine", [(V.VP_PREC_FP64, None), (V.VP_PREC_SPLIT, None),
+                                              (V.VP_PREC_SPLIT, V.ENGINE_TCGEN05)])
+def test_batch_graph_matches_single_tree_evaluations(precision, engine):
     import torch
     ws = _workloads()
     vps = [V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, precision=precision) for w in ws]
     try:
+        if engine is not None:
+            for vp in vps:
+                V.vp_tree_set_engine(vp.tree, engine)
         fs = [torch.from_numpy(w.f).cuda() for w in ws]
         singles = [vp(f) for vp, f in zip(vps, fs)]
         us = [torch.full_like(f, float("nan")) for f in fs]
