@@ -1,12 +1,14 @@
 """Learned warm start for the per-step boundary integral equation.
 
 A sequence of steps n = 0, 1, ... each solves (1/2 + D + W) mu_n = g_n by GMRES (library). The
-network (library kernels) sees the last three densities, the current boundary data and the residual
-of the cubic extrapolation 3 mu_{n-1} - 3 mu_{n-2} + mu_{n-3} (one operator apply), all scaled by
-fixed factors, and predicts the correction to that extrapolation; its output, scaled back and added
-to the extrapolation, is the initial guess. It is
-trained on densities that plain (cold-start) GMRES solves produce. Plain GMRES to the same residual
-stays the solver and the judge of the result: the guess only changes where GMRES starts.
+network (library kernels) sees the last density, its first and second backward differences, the
+current boundary data and the residual of the quadratic extrapolation 3 mu_{n-1} - 3 mu_{n-2} +
+mu_{n-3} (one operator apply), each over a fixed scale, and predicts the correction to that
+extrapolation. The correction is used either added to the extrapolation as the initial guess (kept
+only if its residual is smaller) or as an augmentation direction of GMRES started at the
+extrapolation (bie_solve_aug). The network is trained on densities that plain (cold-start) GMRES
+solves produce. Plain GMRES to the same residual stays the solver and decides when the result is
+accurate enough: the network only changes where, and along which extra direction, GMRES starts.
 """
 from __future__ import annotations
 
