@@ -56,7 +56,7 @@ def residuals(bie, mus, G, idx):
 def _features(mus, G, R, n, scale):
     """Network inputs [B][10][N] for steps n (index tensor), formed in FP64 and then rounded to FP32:
     the last density, its first and second backward differences, the boundary data and the residual
-    R of the cubic extrapolation (rows matching n), each over its own fixed scale (differences are
+    R of the quadratic extrapolation (rows matching n), each over its own fixed scale (differences are
     scaled separately so that FP32 keeps them); and the extrapolation itself [B][2N]."""
     import torch
     N = mus.shape[1] // 2
