@@ -403,13 +403,15 @@ def run_steps(args):
             "config": {"workload": wl.name, "alpha": wl.alpha, "boundary_nodes": r["nodes"],
                        "volume_nodes": r["volume_nodes"], "volume_precision": "fp64" if prec == V.VP_PREC_FP64 else "split",
                        "train_steps": args.train_steps, "test_steps": args.test_steps, "epochs": args.epochs,
-                       "gmres_tol": 1e-11, "net": "circular conv1d 10-64-64-64-2, kernel 9, fp32"},
+                       "gmres_tol": 1e-11, "net": "circular conv1d 10-64-64-64-2 (network) and 12-64-64-64-2 (network4), kernel 9, fp32"},
             "held_out": ev,
             "iterations_saved_vs_cold": ev["cold"]["mean_iters"] - ev["network"]["mean_iters"],
             "iterations_saved_vs_extrapolation": ev["extrapolation"]["mean_iters"] - ev["network"]["mean_iters"],
             "augmented_iterations_saved_vs_cold": ev["cold"]["mean_iters"] - ev["network_aug"]["mean_iters"],
             "augmented_iterations_saved_vs_extrapolation":
                 ev["extrapolation"]["mean_iters"] - ev["network_aug"]["mean_iters"],
+            "network4_iterations_saved_vs_cubic": (ev["cubic"]["mean_iters"] - ev["network4"]["mean_iters"])
+            if "network4" in ev else None,
             "plain_mean_iters": r["plain_mean_iters"], "volume_ms_mean": r["volume_ms_mean"],
             "train_seconds": r["train_seconds"], "train_loss": [r["first_train_loss"], r["final_train_loss"]],
             "interior_rel_err_exact_solution": err, "wall_seconds": wall,

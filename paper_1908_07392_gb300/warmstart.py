@@ -43,50 +43,72 @@ def plain_solves(bie, G, tol):
     return torch.stack(mus), its
 
 
-def _extrapolation(mus, n):
-    return 3 * mus[n - 1] - 3 * mus[n - 2] + mus[n - 3]
+# weights of mu_{n-1}, mu_{n-2}, ... in the extrapolation through the last `order` densities
+_EXTRAP = {3: (3.0, -3.0, 1.0), 4: (4.0, -6.0, 4.0, -1.0)}
 
 
-def residuals(bie, mus, G, idx):
-    """r_n = g_n - A (3 mu_{n-1} - 3 mu_{n-2} + mu_{n-3}) for the steps idx ([len(idx)][2N])."""
+def _extrapolation(mus, n, order=3):
+    return sum(c * mus[n - 1 - k] for k, c in enumerate(_EXTRAP[order]))
+
+
+def in_channels(order=3):
+    """Network inputs: the last density, its backward differences up to order - 1, g_n and r_n."""
+    return 2 * (order + 2)
+
+
+def residuals(bie, mus, G, idx, order=3):
+    """r_n = g_n - A (extrapolation of mu_n from the last `order` densities) for the steps idx."""
     import torch
-    return torch.stack([G[n] - bie.apply(_extrapolation(mus, n)) for n in idx])
+    return torch.stack([G[n] - bie.apply(_extrapolation(mus, n, order)) for n in idx])
+
+
+def _differences(mus, n, order):
+    """mu_{n-1} and its backward differences of order 1 .. order-1 (FP64)."""
+    lags = [mus[n - 1 - k] for k in range(order)]
+    out = [lags[0]]
+    cur = lags
+    for _ in range(order - 1):
+        cur = [cur[k] - cur[k + 1] for k in range(len(cur) - 1)]
+        out.append(cur[0])
+    return out
 
 
 def _features(mus, G, R, n, scale):
-    """Network inputs [B][10][N] for steps n (index tensor), formed in FP64 and then rounded to FP32:
-    the last density, its first and second backward differences, the boundary data and the residual
-    R of the quadratic extrapolation (rows matching n), each over its own fixed scale (differences are
-    scaled separately so that FP32 keeps them); and the extrapolation itself [B][2N]."""
+    """Network inputs [B][2 (order + 2)][N] for steps n (index tensor), formed in FP64 and then
+    rounded to FP32: the last density, its backward differences, the boundary data and the residual R
+    of the extrapolation (rows matching n), each over its own fixed scale (differences are scaled
+    separately so that FP32 keeps them); and the extrapolation itself [B][2N]."""
     import torch
+    order = scale["order"]
     N = mus.shape[1] // 2
-    m1, m2, m3 = mus[n - 1], mus[n - 2], mus[n - 3]
-    parts = [(m1, "s_mu"), (m1 - m2, "s_d1"), (m1 - 2 * m2 + m3, "s_d2"), (G[n], "s_g"), (R, "s_r")]
+    parts = [(v, f"s_d{k}") for k, v in enumerate(_differences(mus, n, order))] + [(G[n], "s_g"), (R, "s_r")]
     ch = [(v / scale[k]).reshape(-1, N, 2).permute(0, 2, 1) for v, k in parts]
     x = torch.cat(ch, dim=1).float().contiguous()
-    return x, _extrapolation(mus, n)
+    return x, _extrapolation(mus, n, order)
 
 
-IN_CHANNELS = 10
+IN_CHANNELS = in_channels(3)
 
 
-def train(bie, net, mus, G, train_idx, epochs=40, batch=16, lr=1e-3, seed=0):
+def train(bie, net, mus, G, train_idx, epochs=40, batch=16, lr=1e-3, seed=0, order=3):
+    """Adam on the network's correction to the extrapolation through the last `order` densities
+    (train_idx >= order)."""
     import torch
     N = mus.shape[1] // 2
     R = torch.zeros_like(mus)
-    R[train_idx] = residuals(bie, mus, G, train_idx)
-    err = mus[train_idx] - _extrapolation(mus, train_idx)
-    d1 = mus[train_idx - 1] - mus[train_idx - 2]
-    d2 = mus[train_idx - 1] - 2 * mus[train_idx - 2] + mus[train_idx - 3]
-    scale = {k: (float(v.std()) or 1.0) for k, v in
-             (("s_mu", mus[train_idx]), ("s_d1", d1), ("s_d2", d2), ("s_g", G[train_idx]), ("s_r", R[train_idx]),
-              ("s_err", err))}
+    R[train_idx] = residuals(bie, mus, G, train_idx, order)
+    err = mus[train_idx] - _extrapolation(mus, train_idx, order)
+    scale = {"order": order}
+    for k, v in enumerate(_differences(mus, train_idx, order)):
+        scale[f"s_d{k}"] = float(v.std()) or 1.0
+    for k, v in (("s_g", G[train_idx]), ("s_r", R[train_idx]), ("s_err", err)):
+        scale[k] = float(v.std()) or 1.0
     rng = np.random.default_rng(seed)
     losses = []
     for ep in range(epochs):
-        order = rng.permutation(train_idx)
-        for k in range(0, len(order) - batch + 1, batch):
-            n = torch.tensor(order[k:k + batch], device="cuda")
+        perm = rng.permutation(train_idx)
+        for k in range(0, len(perm) - batch + 1, batch):
+            n = torch.tensor(perm[k:k + batch], device="cuda")
             x, ext = _features(mus, G, R[n], n, scale)
             t = ((mus[n] - ext).reshape(-1, N, 2).permute(0, 2, 1) / scale["s_err"]).float().contiguous()
             losses.append(net.train_step(x, t, lr))
@@ -98,7 +120,7 @@ def correction(bie, net, scale, mus, G, n):
     extrapolation's residual."""
     import torch
     idx = torch.tensor([n], device="cuda")
-    r = residuals(bie, mus, G, [n])
+    r = residuals(bie, mus, G, [n], scale["order"])
     x, ext = _features(mus, G, r, idx, scale)
     y = net.forward(x)[0]                                   # [2][N]
     return ext[0], scale["s_err"] * y.permute(1, 0).reshape(-1).double(), r[0]
@@ -117,63 +139,90 @@ def guess(bie, net, scale, mus, G, n):
     return ext, False, ratio
 
 
-def evaluate(bie, net, scale, mus, G, test_idx, tol, rhs=None):
-    """GMRES iterations and solve times from each initial guess on the held-out steps. With rhs
-    (n -> (g_n, ms)), the right-hand side is recomputed per step and its time added to every method."""
+def evaluate(bie, nets, mus, G, test_idx, tol, rhs=None):
+    """GMRES iterations and solve times from each initial guess on the held-out steps: cold, previous
+    density, extrapolation through the last 3 and 4 densities, and for every (name -> (net, scale))
+    in nets the network's guess ("name") and its correction as an augmentation direction
+    ("name_aug"). With rhs (n -> (g_n, ms)), the right-hand side is recomputed per step and its time
+    added to every method."""
     import torch
-    res = {k: {"iters": [], "ms": []} for k in ("cold", "previous", "extrapolation", "network", "network_aug")}
-    kept, ratios = 0, []
+    names = ["cold", "previous", "extrapolation", "cubic"]
+    for nm in nets:
+        names += [nm, nm + "_aug"]
+    res = {k: {"iters": [], "ms": []} for k in names}
+    kept = {nm: 0 for nm in nets}
+    ratios = {nm: [] for nm in nets}
     # one untimed pass through every path first (library and torch kernels load on first use)
     n0 = test_idx[0]
     (G[n0], 0.0) if rhs is None else rhs(n0)
-    g0, _, _ = guess(bie, net, scale, mus, G, n0)
-    bie.solve(G[n0], g0, tol)
-    e0, d0, _ = correction(bie, net, scale, mus, G, n0)
-    bie.solve(G[n0], e0, tol, aug=d0)
+    for net, scale in nets.values():
+        g0, _, _ = guess(bie, net, scale, mus, G, n0)
+        bie.solve(G[n0], g0, tol)
+        e0, d0, _ = correction(bie, net, scale, mus, G, n0)
+        bie.solve(G[n0], e0, tol, aug=d0)
     torch.cuda.synchronize()
-    for n in test_idx:
-        g, t_rhs = (G[n], 0.0) if rhs is None else rhs(n)
-        guesses = {
-            "cold": None,
-            "previous": mus[n - 1],
-            "extrapolation": _extrapolation(mus, n),
-        }
+
+    def solve(name, x0, extra_s, t_rhs, aug=None):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        guesses["network"], used, ratio = guess(bie, net, scale, mus, G, n)
-        kept += int(used)
-        ratios.append(ratio)
-        torch.cuda.synchronize()
-        t_net = time.perf_counter() - t0
-        for k, x0 in guesses.items():
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            mu, it, rr = bie.solve(g, x0, tol)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0 + (t_net if k == "network" else 0.0) + t_rhs / 1000.0
-            if not rr <= 10 * tol:
-                raise RuntimeError(f"GMRES from the {k} guess did not reach the tolerance ({rr:.2e})")
-            res[k]["iters"].append(it)
-            res[k]["ms"].append(1000 * dt)
-        # the network's correction as an augmentation direction of GMRES started at the extrapolation
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ext, d, _ = correction(bie, net, scale, mus, G, n)
-        mu, it, rr = bie.solve(g, ext, tol, aug=d)
+        mu, it, rr = bie.solve(g, x0, tol, aug=aug)
         torch.cuda.synchronize()
         if not rr <= 10 * tol:
-            raise RuntimeError(f"augmented GMRES did not reach the tolerance ({rr:.2e})")
-        res["network_aug"]["iters"].append(it)
-        res["network_aug"]["ms"].append(1000 * (time.perf_counter() - t0) + t_rhs)
+            raise RuntimeError(f"GMRES ({name}) did not reach the tolerance ({rr:.2e})")
+        res[name]["iters"].append(it)
+        res[name]["ms"].append(1000 * (time.perf_counter() - t0 + extra_s) + t_rhs)
+
+    for n in test_idx:
+        g, t_rhs = (G[n], 0.0) if rhs is None else rhs(n)
+        solve("cold", None, 0.0, t_rhs)
+        solve("previous", mus[n - 1], 0.0, t_rhs)
+        solve("extrapolation", _extrapolation(mus, n, 3), 0.0, t_rhs)
+        solve("cubic", _extrapolation(mus, n, 4), 0.0, t_rhs)
+        for nm, (net, scale) in nets.items():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x0, used, ratio = guess(bie, net, scale, mus, G, n)
+            torch.cuda.synchronize()
+            kept[nm] += int(used)
+            ratios[nm].append(ratio)
+            solve(nm, x0, time.perf_counter() - t0, t_rhs)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ext, d, _ = correction(bie, net, scale, mus, G, n)
+            torch.cuda.synchronize()
+            solve(nm + "_aug", ext, time.perf_counter() - t0, t_rhs, aug=d)
     out = {k: {"mean_iters": float(np.mean(v["iters"])), "max_iters": int(np.max(v["iters"])),
                "mean_ms": float(np.mean(v["ms"]))} for k, v in res.items()}
-    out["network"]["kept_fraction"] = kept / max(1, len(test_idx))
-    out["network"]["residual_ratio_vs_extrapolation"] = float(np.exp(np.mean(np.log(ratios))))
+    for nm in nets:
+        out[nm]["kept_fraction"] = kept[nm] / max(1, len(test_idx))
+        out[nm]["residual_ratio_vs_extrapolation"] = float(np.exp(np.mean(np.log(ratios[nm]))))
     return out
 
 
+def _train_nets(bie, mus, G, n_train, orders, epochs, batch, lr, seed, width, n_layers, ksize):
+    """One network per extrapolation order: "network" corrects the extrapolation through the last 3
+    densities, "network4" the one through the last 4. Returns ({name: (net, scale)}, seconds, the
+    first network's scale)."""
+    nets = {}
+    t0 = time.perf_counter()
+    try:
+        for order in orders:
+            net = WarmStartNet(in_ch=in_channels(order), width=width, out_ch=2, n_layers=n_layers, ksize=ksize,
+                               n=bie.N, max_batch=batch, seed=seed)
+            nets["network" if order == 3 else f"network{order}"] = (net, None)
+            scale = train(bie, net, mus, G, np.arange(order, 3 + n_train), epochs=epochs, batch=batch, lr=lr,
+                          seed=seed, order=order)
+            nets["network" if order == 3 else f"network{order}"] = (net, scale)
+    except Exception:
+        for net, _ in nets.values():
+            net.close()
+        raise
+    first = next(iter(nets.values()))[1]
+    return nets, time.perf_counter() - t0, first
+
+
 def experiment(alpha, n_panels=256, n_train=2000, n_test=200, dt=1e-3, tol=1e-11, epochs=40, batch=16,
-               lr=1e-3, seed=5, width=64, n_layers=4, ksize=9):
+               lr=1e-3, seed=5, width=64, n_layers=4, ksize=9, orders=(3,)):
     """Plain solves for n_train + n_test + 3 steps of a star with moving exterior forcing, network
     training on the first n_train, iterations and times from each initial guess on the rest."""
     rng = np.random.default_rng(seed)
@@ -186,16 +235,14 @@ def experiment(alpha, n_panels=256, n_train=2000, n_test=200, dt=1e-3, tol=1e-11
         G = boundary_data(bie, forcing, times)
         mus, its = plain_solves(bie, G, tol)
         t_plain = time.perf_counter() - t0
-        net = WarmStartNet(in_ch=IN_CHANNELS, width=width, out_ch=2, n_layers=n_layers, ksize=ksize, n=bie.N,
-                           max_batch=batch, seed=seed)
+        nets, t_train, scale = _train_nets(bie, mus, G, n_train, orders, epochs, batch, lr, seed, width, n_layers,
+                                           ksize)
         try:
-            t0 = time.perf_counter()
-            scale = train(bie, net, mus, G, np.arange(3, 3 + n_train), epochs=epochs, batch=batch, lr=lr, seed=seed)
-            t_train = time.perf_counter() - t0
             test_idx = np.arange(3 + n_train, steps)
-            ev = evaluate(bie, net, scale, mus, G, test_idx, tol)
+            ev = evaluate(bie, nets, mus, G, test_idx, tol)
         finally:
-            net.close()
+            for net, _ in nets.values():
+                net.close()
         return {"nodes": bie.N, "alpha": alpha, "n_train": n_train, "n_test": n_test, "tol": tol,
                 "plain_mean_iters": float(np.mean(its)), "plain_seconds": t_plain, "train_seconds": t_train,
                 "final_train_loss": float(np.mean(scale["losses"][-20:])), "first_train_loss": float(scale["losses"][0]),
@@ -243,7 +290,7 @@ class StepProblem:
 
 
 def step_experiment(wl, n_panels=256, n_train=2000, n_test=200, tol=1e-11, precision=VP_PREC_FP64, epochs=40,
-                    batch=16, lr=1e-3, seed=5, width=64, n_layers=4, ksize=9, log=None):
+                    batch=16, lr=1e-3, seed=5, width=64, n_layers=4, ksize=9, log=None, orders=(3, 4)):
     """Steps of the coupled problem: plain solves for n_train + n_test + 3 steps, network training on
     the first n_train, then per held-out step the volume potential, its boundary trace and GMRES from
     each initial guess (step time = volume part + guess + GMRES)."""
@@ -268,18 +315,16 @@ def step_experiment(wl, n_panels=256, n_train=2000, n_test=200, tol=1e-11, preci
         t_plain = time.perf_counter() - t0
         if log:
             log(f"plain solves: mean {np.mean(its):.1f} iterations, {t_plain:.1f} s")
-        net = WarmStartNet(in_ch=IN_CHANNELS, width=width, out_ch=2, n_layers=n_layers, ksize=ksize, n=bie.N,
-                           max_batch=batch, seed=seed)
+        nets, t_train, scale = _train_nets(bie, mus, G, n_train, orders, epochs, batch, lr, seed, width, n_layers,
+                                           ksize)
         try:
-            t0 = time.perf_counter()
-            scale = train(bie, net, mus, G, np.arange(3, 3 + n_train), epochs=epochs, batch=batch, lr=lr, seed=seed)
-            t_train = time.perf_counter() - t0
             if log:
                 log(f"training: {t_train:.1f} s, loss {scale['losses'][0]:.3e} -> {np.mean(scale['losses'][-20:]):.3e}")
             test_idx = np.arange(3 + n_train, steps)
-            ev = evaluate(bie, net, scale, mus, G, test_idx, tol, rhs=lambda n: prob.rhs(float(times[n])))
+            ev = evaluate(bie, nets, mus, G, test_idx, tol, rhs=lambda n: prob.rhs(float(times[n])))
         finally:
-            net.close()
+            for net, _ in nets.values():
+                net.close()
         return {"nodes": bie.N, "volume_nodes": prob.vp.N, "alpha": wl.alpha, "n_train": n_train, "n_test": n_test,
                 "tol": tol, "plain_mean_iters": float(np.mean(its)), "rhs_seconds": t_rhs,
                 "volume_ms_mean": float(np.mean(vp_ms[3:])), "plain_seconds": t_plain, "train_seconds": t_train,
