@@ -137,9 +137,20 @@ def cpu_sample(w, budget_s, seed=0):
     n = int(max(cores, min(4096, budget_s / one * cores * 0.8)))
     idx = rng.choice(w.n_nodes, n, replace=False)
     t0 = time.perf_counter()
-    oracle.volume_potential(w.kernel, w.alpha, w.p, w.tree, w.f, X[idx], Y[idx])
+    vals = oracle.volume_potential(w.kernel, w.alpha, w.p, w.tree, w.f, X[idx], Y[idx])
     dt = time.perf_counter() - t0
+    cpu_sample.last = (idx, vals)   # sampled nodes and the oracle's (u, du/dx, du/dy) there
     return n / dt, n, cores, dt
+
+
+def sampled_errors(idx, vals, u, g):
+    """Per-field relative max-norm error of the GPU result on the sampled nodes (u, gradu host)."""
+    import numpy as np
+    out = {}
+    for name, a, b in (("u", u[idx], vals[0]), ("dudx", g[0][idx], vals[1]), ("dudy", g[1][idx], vals[2])):
+        out[name] = float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+    out["nodes"] = int(len(idx))
+    return out
 
 
 class ClockSampler:
@@ -501,6 +512,7 @@ def measure(args, V, w, prec, world, local, with_e2e):
                     "fp64_equivalent_tflops": near_flops / (near_ms / 1000.0) / 1e12}
             traffic = None
         return {"value": value, "total_ms": total_ms, "N": N, "setup_s": setup_s, "n_tc": n_tc,
+                "u": u.cpu().numpy(), "g": g.cpu().numpy(),
                 "launches": int(launches), "e2e": e2e, "clocks": sampler.summary(),
                 "stage_ms": {name: round(statistics.mean(m[k] for m in stage_ms), 4)
                              for k, name in enumerate(V.STAGE_NAMES)},
@@ -533,15 +545,22 @@ def main():
     B.build()
     w = workload(args.alpha, args.max_depth)
     # headline form: split precision unless only FP64 is asked for; "both" adds the FP64 form beside it
-    head_prec = V.VP_PREC_FP64 if args.precision == "fp64" else V.VP_PREC_SPLIT
-    head = measure(args, V, w, head_prec, world, local, not args.no_e2e)
-    plain = measure(args, V, w, V.VP_PREC_FP64, world, local, False) if args.precision == "both" else None
-
+    # the CPU baseline (the oracle on a bounded sample of nodes) runs first; its values also give the
+    # sampled error of every GPU form measured below
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, n, cores, dt = cpu_sample(w, args.cpu_seconds)
         cpu = {"value": rate, "unit": "nodes/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} random target nodes of the same workload, {dt:.1f} s on {cores} threads"}
+    head_prec = V.VP_PREC_FP64 if args.precision == "fp64" else V.VP_PREC_SPLIT
+    head = measure(args, V, w, head_prec, world, local, not args.no_e2e)
+    plain = measure(args, V, w, V.VP_PREC_FP64, world, local, False) if args.precision == "both" else None
+    errs = {}
+    if cpu is not None:
+        idx, vals = cpu_sample.last
+        errs["split" if head_prec == V.VP_PREC_SPLIT else "fp64"] = sampled_errors(idx, vals, head["u"], head["g"])
+        if plain is not None:
+            errs["fp64"] = sampled_errors(idx, vals, plain["u"], plain["g"])
 
     if rank == 0:
         split = head_prec == V.VP_PREC_SPLIT
@@ -561,6 +580,7 @@ def main():
                                 "vp_eval, which overlaps the near field with the far-field chain",
                 "roofline": head["roofline"],
                 "cpu_baseline": cpu,
+                "rel_err_vs_oracle_sampled": errs or None,
                 "e2e": head["e2e"],
                 "gpu_launches": head["launches"] * args.steps,
                 "clocks": head["clocks"]}
