@@ -183,3 +183,46 @@ def test_brute_force_single_leaf(kind):
                 total += si.dblquad(lambda yv, xv: G(np.hypot(x0 - xv, y0 - yv)) * ftilde(yv, xv),
                                     a, b, cc, d, epsabs=1e-14, epsrel=1e-12)[0]
         assert abs(u[0] - total) <= 1e-10 * max(abs(total), 1e-3)
+
+
+def _diff_matrix(x):
+    """First-derivative matrix of the Lagrange interpolant on the nodes x (barycentric form)."""
+    n = len(x)
+    w = np.array([1.0 / np.prod([x[j] - x[k] for k in range(n) if k != j]) for j in range(n)])
+    D = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                D[i, j] = (w[j] / w[i]) / (x[i] - x[j])
+        D[i, i] = -D[i].sum()
+    return D
+
+
+@pytest.mark.parametrize("kind,tol", [(I.KERNEL_MHELMHOLTZ, 5e-7), (I.KERNEL_MBIHARMONIC, 2e-4)])
+def test_pde_applied_back_by_spectral_differentiation(kind, tol):
+    # On a leaf away from the box edge, the potential solves (alpha^2 - Lap) u = f (G1) or
+    # Lap (alpha^2 - Lap) u = f (G2): apply the operator to the oracle's u at the leaf's nodes with
+    # the p x p Lagrange differentiation matrices and compare with f (the source there is smooth, so
+    # the leaf polynomial of u is accurate to the tolerance)
+    p, alpha = 14, 4.0
+    tree = I.uniform_tree(2, side=2.0)                 # 16 leaves of side 0.5
+    fn = I.gaussian_sum([[0.1, -0.05]], [0.35], [1.0])
+    X, Y = I.node_coords(tree, p)
+    f = fn(X, Y)
+    leaf = 5                                            # interior leaf (level 2, ix = 1, iy = 1)
+    assert tree.ix[leaf] == 1 and tree.iy[leaf] == 1
+    idx = leaf * p * p + np.arange(p * p)
+    u, _, _ = O.volume_potential(kind, alpha, p, tree, f, X[idx], Y[idx])
+    xi, _ = I.gl_nodes(p)
+    h = tree.side / 2 ** tree.level[leaf]
+    D = _diff_matrix(xi) * (2.0 / h)
+    U = u.reshape(p, p)                                 # [j (y)][i (x)]
+
+    def lap(V):
+        return V @ (D @ D).T + (D @ D) @ V
+
+    op = alpha ** 2 * U - lap(U)
+    if kind == I.KERNEL_MBIHARMONIC:
+        op = lap(op)
+    F = f[idx].reshape(p, p)
+    assert np.abs(op - F).max() <= tol * np.abs(F).max()
