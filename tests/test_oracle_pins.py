@@ -226,3 +226,40 @@ def test_pde_applied_back_by_spectral_differentiation(kind, tol):
         op = lap(op)
     F = f[idx].reshape(p, p)
     assert np.abs(op - F).max() <= tol * np.abs(F).max()
+
+
+def test_brute_force_four_leaves():
+    # Four leaves (uniform depth 1, side 1), p = 4, a random source per leaf: targets next to the
+    # corner the leaves share and inside one leaf, against adaptive scipy quadrature of each leaf's
+    # interpolant, split at the target's coordinates
+    alpha, p = 5.0, 4
+    tree = I.uniform_tree(1, side=1.0)
+    rng = np.random.default_rng(21)
+    f = rng.uniform(-1, 1, tree.level.size * p * p)
+    xi, _ = np.polynomial.legendre.leggauss(p)
+    V = np.vander(xi, p, increasing=True)
+
+    def G(r):
+        return sp.k0(alpha * r) / (2 * np.pi)
+
+    targets = [(0.011, -0.023), (-0.31, 0.17)]
+    for (x0, y0) in targets:
+        u, _, _ = O.volume_potential(0, alpha, p, tree, f, np.array([x0]), np.array([y0]))
+        total = 0.0
+        for leaf in range(tree.level.size):
+            h = 0.5
+            lx, ly = -0.5 + tree.ix[leaf] * h, -0.5 + tree.iy[leaf] * h
+            F = f[leaf * p * p:(leaf + 1) * p * p].reshape(p, p)
+            Cm = np.linalg.solve(V, np.linalg.solve(V, F).T)
+            cx, cy = lx + h / 2, ly + h / 2
+
+            def integrand(yv, xv, Cm=Cm, cx=cx, cy=cy):
+                s = np.polynomial.polynomial.polyval2d(2 * (xv - cx) / h, 2 * (yv - cy) / h, Cm)
+                return G(np.hypot(x0 - xv, y0 - yv)) * s
+
+            xs = sorted({lx, lx + h} | ({x0} if lx < x0 < lx + h else set()))
+            ys = sorted({ly, ly + h} | ({y0} if ly < y0 < ly + h else set()))
+            for a, b in zip(xs[:-1], xs[1:]):
+                for c, d in zip(ys[:-1], ys[1:]):
+                    total += si.dblquad(integrand, a, b, c, d, epsabs=1e-14, epsrel=1e-12)[0]
+        assert abs(u[0] - total) <= 1e-10 * max(abs(total), 1e-3)
