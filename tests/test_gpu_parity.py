@@ -128,3 +128,53 @@ def test_errors_from_the_device_entry_points():
         with pytest.raises(V.VPError) as e:
             V.vp_tables_build(**args)
         assert e.value.code == -1
+
+
+def _quarter_turn_symmetric_tree(seed):
+    """An adaptive, 2:1-balanced tree that a quarter turn about the root centre maps onto itself:
+    random level-2 and level-3 splits, closed under the rotation (l, ix, iy) -> (l, 2^l-1-iy, ix)."""
+    rng = np.random.default_rng(seed)
+    rot = lambda b: (b[0], (1 << b[0]) - 1 - b[2], b[1])
+    leaves = {(2, x, y) for x in range(4) for y in range(4)}
+    for level in (2, 3):
+        cand = sorted(b for b in leaves if b[0] == level)
+        for b in [cand[k] for k in rng.choice(len(cand), 2, replace=False)]:
+            orbit = {b, rot(b), rot(rot(b)), rot(rot(rot(b)))}
+            for o in orbit:
+                if o in leaves:
+                    leaves.discard(o)
+                    leaves.update(I._children(*o))
+        leaves = I.balance_21(leaves)
+    assert leaves == {rot(b) for b in leaves}
+    return I.tree_from_set(leaves, 0.0, 0.0, 2.0)
+
+
+@pytest.mark.parametrize("shape,kernel,precision,tol", [
+    ("uniform", 0, V.VP_PREC_FP64, 1e-12), ("uniform", 1, V.VP_PREC_FP64, 1e-12),
+    ("uniform", 0, V.VP_PREC_SPLIT, 1e-9), ("uniform", 1, V.VP_PREC_SPLIT, 1e-9),
+    ("adaptive", 1, V.VP_PREC_FP64, 1e-12), ("adaptive", 0, V.VP_PREC_SPLIT, 1e-9)])
+def test_quarter_turn_symmetry(shape, kernel, precision, tol):
+    # The kernels are rotation invariant and the tree, centred at the origin, maps onto itself under
+    # a quarter turn R, so the source f(R^-1 x) has the potential u(R^-1 x) and the gradient
+    # R grad u(R^-1 x) exactly: every relative-position table and expansion operator (near, V, and
+    # on the adaptive tree the W and X lists) must agree with its rotated counterpart
+    import torch
+    p = 8
+    tree = I.uniform_tree(3, side=2.0) if shape == "uniform" else _quarter_turn_symmetric_tree(4)
+    X, Y = I.node_coords(tree, p)
+    rng = np.random.default_rng(8)
+    fn = I.gaussian_sum(rng.uniform(-0.6, 0.6, (3, 2)), rng.uniform(0.15, 0.3, 3), rng.uniform(-1, 1, 3))
+    f = fn(X, Y)
+    # m[k]: index of the node at R^-1 x_k = (y_k, -x_k)
+    key = {(round(x, 9), round(y, 9)): k for k, (x, y) in enumerate(zip(X, Y))}
+    m = np.array([key[(round(y, 9), round(-x, 9))] for x, y in zip(X, Y)])
+    vp = V.VolumePotential(kernel, 10.0, p, tree, precision=precision)
+    try:
+        u1, g1 = vp(torch.from_numpy(f).cuda())
+        u2, g2 = vp(torch.from_numpy(np.ascontiguousarray(f[m])).cuda())
+        u1, g1, u2, g2 = (t.cpu().numpy() for t in (u1, g1, u2, g2))
+    finally:
+        vp.close()
+    assert rel_err(u2, u1[m]) < tol
+    # R (a, b) = (-b, a)
+    assert rel_err(g2[0], -g1[1][m]) < tol and rel_err(g2[1], g1[0][m]) < tol
