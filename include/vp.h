@@ -175,6 +175,20 @@ int vp_eval(vp_tree tree, const double* f, double* u, double* gradu, void* strea
  */
 int vp_eval_host(vp_tree tree, const double* f, double* u, double* gradu, void* stream);
 
+/*
+ * vp_special -- the device special functions the tables and expansion operators are built from,
+ * evaluated at `count` arguments z (device array) for checks against reference values:
+ *  which 0: out [2][count] = e^z K0(z), e^z K1(z) (small-argument series of App. C for z <= 2,
+ *           the integral representation by the trapezoidal rule for 2 < z <= 25, the Hankel
+ *           expansion beyond);
+ *  which 1: out [nmax+1][count] = e^z Khat_n(z), Khat_n = K_n(z) (z/2)^n 2/(n-1)! (n >= 1),
+ *           Khat_0 = K0 -- the normalised multipole basis of Sec. 3.2.1 (Eq. mpole);
+ *  which 2: out [nmax+1][count] = Ihat_n(z) = I_n(z) n!/(z/2)^n -- the normalised local basis
+ *           (Eq. loc); meant for the arguments the expansions use (z up to about 50).
+ * 1 <= nmax <= 64 for which 1 and 2. Errors: VP_ERR_ARG, VP_ERR_CUDA.
+ */
+int vp_special(int which, int nmax, int count, const double* z, double* out, void* stream);
+
 /* Stages of one evaluation, for vp_eval_timed and vp_tree_stats. */
 enum {
   VP_STAGE_UPWARD = 0,   /* clear, source-to-multipole, multipole-to-multipole */
@@ -259,6 +273,15 @@ int vp_tree_set_engine(vp_tree tree, int engine);
 int vp_autotune(vp_tree tree, const double* f, double* u, double* gradu, const char* cache_path, void* stream,
                 int* n_tcgen05);
 int vp_device_status(void);
+
+/*
+ * vp_selftest_timeout -- exercises the give-up path of the bounded device waits: a one-thread
+ * kernel waits on an mbarrier that nothing arrives at, gives up after about two million clocks
+ * (about a millisecond), raises the device flag and returns; the call synchronises `stream` and
+ * returns what vp_device_status then reports: VP_ERR_TIMEOUT when the path works (the flag is
+ * cleared again). The device stays usable afterwards.
+ */
+int vp_selftest_timeout(void* stream);
 
 /*
  * Batches -- many independent trees (each with its own tables: kernel, alpha, p and depth may all

@@ -52,6 +52,7 @@ def load_library():
     lib.vp_tree_size.argtypes = [c_void_p, i64p, i64p]
     lib.vp_tree_nodes.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.vp_tree_interp.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p]
+    lib.vp_special.argtypes = [c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]
     lib.vp_eval.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.vp_eval_host.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.vp_tree_free.argtypes = [c_void_p]
@@ -87,6 +88,7 @@ def load_library():
     lib.vp_autotune.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, ctypes.c_char_p, c_void_p,
                                 ctypes.POINTER(c_int)]
     lib.vp_device_status.argtypes = []
+    lib.vp_selftest_timeout.argtypes = [c_void_p]
     lib.vp_last_cuda_error.argtypes = []
     lib.vp_last_cuda_error.restype = ctypes.c_char_p
     lib.vp_plan_pairs.argtypes = [c_int, i32p, i32p, i32p, i64p, i32p, i32p, i32p]
@@ -105,10 +107,10 @@ def load_library():
 
 def exported_symbols():
     """Names declared in include/vp.h (the ABI surface)."""
-    return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_tree_interp", "vp_eval", "vp_eval_host",
+    return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_tree_interp", "vp_special", "vp_eval", "vp_eval_host",
             "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
-            "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status",
+            "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status", "vp_selftest_timeout",
             "bie_create", "bie_free", "bie_size", "bie_nodes", "bie_apply", "bie_solve", "bie_solve_aug", "bie_eval",
             "bie_stokeslets", "bie_kernel_scalars", "ws_create", "ws_free", "ws_num_params", "ws_params",
             "ws_forward", "ws_grad", "ws_train_step"]
@@ -120,6 +122,11 @@ ENGINE_TCGEN05 = 1
 
 def vp_tree_set_engine(tree: int, engine: int):
     _check(load_library().vp_tree_set_engine(ctypes.c_void_p(tree), int(engine)), "vp_tree_set_engine")
+
+
+def vp_selftest_timeout(stream=None) -> int:
+    """Status code of the bounded-wait self test (VP_ERR_TIMEOUT = -7 when the give-up path works)."""
+    return int(load_library().vp_selftest_timeout(_stream_ptr(stream)))
 
 
 def vp_device_status():
@@ -190,6 +197,16 @@ def vp_tree_size(tree: int):
 def vp_tree_nodes(tree: int, xy, stream=None):
     _check(load_library().vp_tree_nodes(ctypes.c_void_p(tree), ctypes.c_void_p(xy.data_ptr()), _stream_ptr(stream)),
            "vp_tree_nodes")
+
+
+def vp_special(which: int, z, nmax: int = 1, stream=None):
+    """Device special functions at z (device float64 [M]); see include/vp.h. Returns [rows][M]."""
+    import torch
+    rows = 2 if which == 0 else nmax + 1
+    out = torch.empty(rows, z.numel(), dtype=torch.float64, device=z.device)
+    _check(load_library().vp_special(int(which), int(nmax), int(z.numel()), ctypes.c_void_p(z.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "vp_special")
+    return out
 
 
 def vp_tree_interp(tree: int, fields, xy, out, stream=None):

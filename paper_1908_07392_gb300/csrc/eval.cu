@@ -1003,6 +1003,12 @@ extern "C" int vp_tree_set_engine(vp_tree tree, int engine) {
   return VP_OK;
 }
 
+extern "C" int vp_selftest_timeout(void* stream) {
+  const int rc = selftest_wait(2000000ll, static_cast<cudaStream_t>(stream));  // about a millisecond
+  if (rc) return rc;
+  return vp_device_status();
+}
+
 extern "C" int vp_device_status(void) {
   int flag = 0;
   const int rc = read_split_error(&flag);

@@ -394,7 +394,8 @@ __device__ inline void umma_commit(unsigned long long* bar) {
 
 // Bounded wait for the completion of phase `parity` of an mbarrier: false if it gave up (~2 s) or
 // if *abort became nonzero meanwhile.
-__device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int* abort = nullptr) {
+__device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity, volatile int* abort = nullptr,
+                                 long long budget = 4000000000ll) {
   const unsigned a = smem_u32(bar);
   const long long t0 = clock64();
   while (true) {
@@ -406,8 +407,18 @@ __device__ inline bool mbar_wait(unsigned long long* bar, unsigned parity, volat
         : "memory");
     if (done) return true;
     if (abort && *abort) return false;
-    if (clock64() - t0 > 4000000000ll) return false;
+    if (clock64() - t0 > budget) return false;
   }
+}
+
+// Exercises the give-up path of the bounded waits: one thread waits on an mbarrier that nothing
+// arrives at, with a budget of `budget` clocks, and raises the same device flag as the GEMM kernel.
+__global__ void k_wait_selftest(long long budget) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n");
+  if (!mbar_wait(&bar, 0, nullptr, budget)) atomicExch(&g_split_error, 1);
 }
 
 // Named barrier 1 over the epilogue warps, returning the AND of `pred` over them (uniform).
@@ -790,6 +801,13 @@ int prepare_split_launch() {
   TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   g_num_sms = sms > 0 ? sms : 1;
   if (dev >= 0 && dev < 64) done[dev] = true;
+  return VP_OK;
+}
+
+int selftest_wait(long long budget, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(budget);
+  TRY(cudaGetLastError());
+  TRY(cudaStreamSynchronize(s));
   return VP_OK;
 }
 

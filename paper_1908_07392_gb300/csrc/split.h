@@ -74,6 +74,8 @@ int prepare_split_launch();
 int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engine, int short_ctas = 0);
 // Read and clear the flag that a bounded wait of the tcgen05 engine gave up.
 int read_split_error(int* flag);
+// Run a kernel whose bounded wait on an mbarrier nothing arrives at gives up after `budget` clocks.
+int selftest_wait(long long budget, cudaStream_t s);
 int launch_slice_list(const double* X, const long long* base, const long long* vid, long long nlist, int K, int kseg,
                       long long seg_stride, long long cstride, void* out, int* eb, cudaStream_t s);
 int launch_reduce_df(const DFReduceArgs& a, int n_dst, cudaStream_t s);

@@ -925,6 +925,41 @@ void gauss_legendre_host(int n, double* x, double* w) { host_gauss_legendre(n, x
 
 }  // namespace vp
 
+namespace vp {
+namespace {
+// One thread per argument: the device special functions, for checks against reference values.
+__global__ void k_special(int which, int nmax, int count, const double* z, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double v[kSpecialMaxOrder + 1];
+  const double x = z[i];
+  if (which == 0) {
+    bessel_k01_scaled(x, v[0], v[1]);
+    out[i] = v[0];
+    out[count + i] = v[1];
+    return;
+  }
+  if (which == 1) khat_scaled(x, nmax, v);
+  else ihat(x, nmax, v);
+  for (int n = 0; n <= nmax; ++n) out[(long long)n * count + i] = v[n];
+}
+}  // namespace
+}  // namespace vp
+
+extern "C" int vp_special(int which, int nmax, int count, const double* z, double* out, void* stream) {
+  if (which < 0 || which > 2 || count < 0 || (count > 0 && (!z || !out)) ||
+      (which > 0 && (nmax < 1 || nmax > vp::kSpecialMaxOrder)))
+    return VP_ERR_ARG;
+  if (count == 0) return VP_OK;
+  vp::k_special<<<(count + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(which, nmax, count, z, out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    vp::set_last_cuda(e);
+    return VP_ERR_CUDA;
+  }
+  return VP_OK;
+}
+
 extern "C" int vp_tables_build(int kernel, double alpha, int p, int levels, double root_side, int order,
                                int precision, void* stream, vp_tables* out) {
   if (!out) return VP_ERR_ARG;

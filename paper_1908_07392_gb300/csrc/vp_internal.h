@@ -15,6 +15,7 @@ constexpr int kNearPos = 33;  // U list: self, 8 same-level, 12 coarser, 12 fine
 constexpr int kWPos = 20;     // W list: level l+1 children of colleagues, not adjacent
 constexpr int kXPos = 20;     // X list: level l-1 leaves adjacent to the parent, not to the box
 constexpr int kVOff = 40;     // V list: same-level offsets in [-3,3]^2 \ [-1,1]^2
+constexpr int kSpecialMaxOrder = 64;  // highest order vp_special evaluates
 
 // Source box relative to a target box [0,1]^2 (units of the target side):
 // lower-left (ox, oy) and side s.

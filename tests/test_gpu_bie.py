@@ -134,3 +134,18 @@ def test_augmented_gmres():
         assert it3 == it4 and torch.equal(mu3, mu4)
     finally:
         b.close()
+
+
+def test_gmres_reports_non_convergence():
+    # an iteration cap below what the tolerance needs: the solver stops there and reports the
+    # iterations and the true residual, which the caller compares with the tolerance
+    import torch
+    b = V.BIE(30.0, n_panels=16)
+    try:
+        g = torch.ones(2 * b.N, dtype=torch.float64, device="cuda")
+        mu, it, rr = b.solve(g, None, 1e-13, max_iter=2)
+        assert it == 2 and rr > 1e-13 and bool(torch.isfinite(mu).all())
+        mu2, it2, rr2 = b.solve(g, mu, 1e-13)
+        assert rr2 < 1e-12
+    finally:
+        b.close()

@@ -110,3 +110,14 @@ def test_overlapped_and_in_order_evaluations_agree_bitwise(precision):
             assert torch.equal(u3, u1) and torch.equal(g3, g1)
     finally:
         vp.close()
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable():
+    # a wait on an mbarrier that nothing arrives at gives up after its budget, raises the device flag
+    # (reported once as VP_ERR_TIMEOUT, then cleared), and later work runs normally
+    import torch
+    assert V.vp_selftest_timeout() == -7
+    V.vp_device_status()          # flag cleared: no error
+    w = I.small_gaussian_workload()
+    (u0, g0), (u1, g1) = _both_engines(w)
+    assert rel_err(u1, u0) < 1e-13 and rel_err(g1, g0) < 1e-13
