@@ -178,3 +178,17 @@ def test_quarter_turn_symmetry(shape, kernel, precision, tol):
     assert rel_err(u2, u1[m]) < tol
     # R (a, b) = (-b, a)
     assert rel_err(g2[0], -g1[1][m]) < tol and rel_err(g2[1], g1[0][m]) < tol
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_single_basis_function_and_constant_sources(kernel):
+    # f = one Lagrange basis function of one leaf: u at every node is that table column (near leaves)
+    # or its expansion (far leaves); f = 1: the sum of all basis functions, the integral of 1
+    rng = np.random.default_rng(17)
+    tree = I.random_balanced_tree(rng, 6, 4, side=2.0, min_depth=2)
+    p = 6
+    N = tree.level.size * p * p
+    k = int(rng.integers(N))
+    for f in (np.eye(1, N, k)[0], np.ones(N)):
+        w = I.Workload("basis", kernel, 12.0, p, tree, f)
+        _check(w)
