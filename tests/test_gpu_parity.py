@@ -192,3 +192,26 @@ def test_single_basis_function_and_constant_sources(kernel):
     for f in (np.eye(1, N, k)[0], np.ones(N)):
         w = I.Workload("basis", kernel, 12.0, p, tree, f)
         _check(w)
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_far_field_truncation_follows_the_expansion_bound(kernel):
+    # the only approximation beyond the tables is the expansion order P: the error against the
+    # oracle falls with P like the separation ratio sqrt(2)/(4 - sqrt(2)) ~ 0.547 of the V lists
+    rng = np.random.default_rng(23)
+    tree = I.random_balanced_tree(rng, 40, 6, side=2.0, min_depth=3)
+    p = 6
+    X, Y = I.node_coords(tree, p)
+    fn = I.gaussian_sum(rng.uniform(-0.6, 0.6, (3, 2)), rng.uniform(0.15, 0.3, 3), rng.uniform(-1, 1, 3))
+    w = I.Workload("trunc", kernel, 3.0, p, tree, fn(X, Y))
+    idx = sample_nodes(w, 300, 3)
+    ou, oux, ouy = oracle_eval(w, idx)
+    errs = {}
+    for P in (8, 16, 24, 40):
+        u, ux, uy = gpu_eval(w, order=P)
+        errs[P] = max(rel_err(u[idx], ou), rel_err(ux[idx], oux), rel_err(uy[idx], ouy))
+    ratio = np.sqrt(2) / (4 - np.sqrt(2))
+    print("error by order", errs)
+    for P, e in errs.items():
+        assert e <= max(10 * ratio ** P, 1e-11), (P, e)
+    assert errs[8] > errs[16] > errs[24]
