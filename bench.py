@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--train-steps", type=int, default=2000, help="steps workload: plain solves to train on")
     ap.add_argument("--test-steps", type=int, default=200, help="steps workload: held-out steps")
     ap.add_argument("--epochs", type=int, default=40, help="steps workload: training epochs")
-    ap.add_argument("--streams", type=int, default=16, help="graph branches for the batched workload")
+    ap.add_argument("--streams", type=int, default=64, help="graph branches for the batched workload")
     ap.add_argument("--engine", default="auto", choices=["auto", "mma", "tcgen05"],
                     help="split-precision GEMM engine: autotuned per launch, mma.sync, or tcgen05")
     return ap.parse_args()
