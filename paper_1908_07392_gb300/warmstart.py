@@ -44,7 +44,7 @@ def plain_solves(bie, G, tol):
 
 
 # weights of mu_{n-1}, mu_{n-2}, ... in the extrapolation through the last `order` densities
-_EXTRAP = {3: (3.0, -3.0, 1.0), 4: (4.0, -6.0, 4.0, -1.0)}
+_EXTRAP = {3: (3.0, -3.0, 1.0), 4: (4.0, -6.0, 4.0, -1.0), 5: (5.0, -10.0, 10.0, -5.0, 1.0)}
 
 
 def _extrapolation(mus, n, order=3):
@@ -141,12 +141,12 @@ def guess(bie, net, scale, mus, G, n):
 
 def evaluate(bie, nets, mus, G, test_idx, tol, rhs=None):
     """GMRES iterations and solve times from each initial guess on the held-out steps: cold, previous
-    density, extrapolation through the last 3 and 4 densities, and for every (name -> (net, scale))
+    density, extrapolation through the last 3, 4 and 5 densities, and for every (name -> (net, scale))
     in nets the network's guess ("name") and its correction as an augmentation direction
     ("name_aug"). With rhs (n -> (g_n, ms)), the right-hand side is recomputed per step and its time
     added to every method."""
     import torch
-    names = ["cold", "previous", "extrapolation", "cubic"]
+    names = ["cold", "previous", "extrapolation", "cubic", "quartic"]
     for nm in nets:
         names += [nm, nm + "_aug"]
     res = {k: {"iters": [], "ms": []} for k in names}
@@ -178,6 +178,7 @@ def evaluate(bie, nets, mus, G, test_idx, tol, rhs=None):
         solve("previous", mus[n - 1], 0.0, t_rhs)
         solve("extrapolation", _extrapolation(mus, n, 3), 0.0, t_rhs)
         solve("cubic", _extrapolation(mus, n, 4), 0.0, t_rhs)
+        solve("quartic", _extrapolation(mus, n, 5), 0.0, t_rhs)
         for nm, (net, scale) in nets.items():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
