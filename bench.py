@@ -414,7 +414,8 @@ def run_steps(args):
             "config": {"workload": wl.name, "alpha": wl.alpha, "boundary_nodes": r["nodes"],
                        "volume_nodes": r["volume_nodes"], "volume_precision": "fp64" if prec == V.VP_PREC_FP64 else "split",
                        "train_steps": args.train_steps, "test_steps": args.test_steps, "epochs": args.epochs,
-                       "gmres_tol": 1e-11, "net": "circular conv1d 10-64-64-64-2 (network) and 12-64-64-64-2 (network4), kernel 9, fp32"},
+                       "gmres_tol": 1e-11, "net": "circular conv1d, fp32: network 10-64-64-64-2 k9 (3 densities), network4 12-64-64-64-2 k9, "
+                              "network8 20-64-64-64-2 k9 (8 densities), temporal8 20-2 k1 (linear filter)"},
             "held_out": ev,
             "iterations_saved_vs_cold": ev["cold"]["mean_iters"] - ev["network"]["mean_iters"],
             "iterations_saved_vs_extrapolation": ev["extrapolation"]["mean_iters"] - ev["network"]["mean_iters"],
@@ -423,6 +424,8 @@ def run_steps(args):
                 ev["extrapolation"]["mean_iters"] - ev["network_aug"]["mean_iters"],
             "network4_iterations_saved_vs_cubic": (ev["cubic"]["mean_iters"] - ev["network4"]["mean_iters"])
             if "network4" in ev else None,
+            "eight_density_iterations_saved_vs_quartic": {
+                k: ev["quartic"]["mean_iters"] - ev[k]["mean_iters"] for k in ("network8", "temporal8") if k in ev},
             "plain_mean_iters": r["plain_mean_iters"], "volume_ms_mean": r["volume_ms_mean"],
             "train_seconds": r["train_seconds"], "train_loss": [r["first_train_loss"], r["final_train_loss"]],
             "interior_rel_err_exact_solution": err, "wall_seconds": wall,

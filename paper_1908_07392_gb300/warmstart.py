@@ -51,9 +51,9 @@ def _extrapolation(mus, n, order=3):
     return sum(c * mus[n - 1 - k] for k, c in enumerate(_EXTRAP[order]))
 
 
-def in_channels(order=3):
-    """Network inputs: the last density, its backward differences up to order - 1, g_n and r_n."""
-    return 2 * (order + 2)
+def in_channels(lags=3):
+    """Network inputs: the last density, its backward differences up to lags - 1, g_n and r_n."""
+    return 2 * (lags + 2)
 
 
 def residuals(bie, mus, G, idx, order=3):
@@ -74,14 +74,15 @@ def _differences(mus, n, order):
 
 
 def _features(mus, G, R, n, scale):
-    """Network inputs [B][2 (order + 2)][N] for steps n (index tensor), formed in FP64 and then
-    rounded to FP32: the last density, its backward differences, the boundary data and the residual R
-    of the extrapolation (rows matching n), each over its own fixed scale (differences are scaled
-    separately so that FP32 keeps them); and the extrapolation itself [B][2N]."""
+    """Network inputs [B][2 (lags + 2)][N] for steps n (index tensor), formed in FP64 and then
+    rounded to FP32: the last density, its backward differences over the last `lags` densities, the
+    boundary data and the residual R of the extrapolation (rows matching n), each over its own fixed
+    scale (differences are scaled separately so that FP32 keeps them); and the extrapolation through
+    the last `order` densities itself [B][2N]."""
     import torch
-    order = scale["order"]
+    order, lags = scale["order"], scale["lags"]
     N = mus.shape[1] // 2
-    parts = [(v, f"s_d{k}") for k, v in enumerate(_differences(mus, n, order))] + [(G[n], "s_g"), (R, "s_r")]
+    parts = [(v, f"s_d{k}") for k, v in enumerate(_differences(mus, n, lags))] + [(G[n], "s_g"), (R, "s_r")]
     ch = [(v / scale[k]).reshape(-1, N, 2).permute(0, 2, 1) for v, k in parts]
     x = torch.cat(ch, dim=1).float().contiguous()
     return x, _extrapolation(mus, n, order)
@@ -90,16 +91,17 @@ def _features(mus, G, R, n, scale):
 IN_CHANNELS = in_channels(3)
 
 
-def train(bie, net, mus, G, train_idx, epochs=40, batch=16, lr=1e-3, seed=0, order=3):
-    """Adam on the network's correction to the extrapolation through the last `order` densities
-    (train_idx >= order)."""
+def train(bie, net, mus, G, train_idx, epochs=40, batch=16, lr=1e-3, seed=0, order=3, lags=None):
+    """Adam on the network's correction to the extrapolation through the last `order` densities, from
+    features of the last `lags` densities (default `order`; train_idx >= both)."""
     import torch
+    lags = order if lags is None else lags
     N = mus.shape[1] // 2
     R = torch.zeros_like(mus)
     R[train_idx] = residuals(bie, mus, G, train_idx, order)
     err = mus[train_idx] - _extrapolation(mus, train_idx, order)
-    scale = {"order": order}
-    for k, v in enumerate(_differences(mus, train_idx, order)):
+    scale = {"order": order, "lags": lags}
+    for k, v in enumerate(_differences(mus, train_idx, lags)):
         scale[f"s_d{k}"] = float(v.std()) or 1.0
     for k, v in (("s_g", G[train_idx]), ("s_r", R[train_idx]), ("s_err", err)):
         scale[k] = float(v.std()) or 1.0
@@ -200,20 +202,27 @@ def evaluate(bie, nets, mus, G, test_idx, tol, rhs=None):
     return out
 
 
-def _train_nets(bie, mus, G, n_train, orders, epochs, batch, lr, seed, width, n_layers, ksize):
-    """One network per extrapolation order: "network" corrects the extrapolation through the last 3
-    densities, "network4" the one through the last 4. Returns ({name: (net, scale)}, seconds, the
-    first network's scale)."""
+# (name, extrapolation order corrected, past densities seen, layers, kernel width, channels)
+SPEC_NETWORK = ("network", 3, 3, 4, 9, 64)            # the configuration's network
+STEP_SPECS = (SPEC_NETWORK,
+              ("network4", 4, 4, 4, 9, 64),           # the same one order up
+              ("network8", 5, 8, 4, 9, 64),           # eight past densities, correcting the quartic
+              ("temporal8", 5, 8, 1, 1, 1))           # a learned linear filter over eight past densities
+
+
+def _train_nets(bie, mus, G, n_train, specs, epochs, batch, lr, seed):
+    """One network per spec (name, order, lags, layers, ksize, width), trained on steps
+    max(order, lags) .. n_train + 2. Returns ({name: (net, scale)}, seconds, the first scale)."""
     nets = {}
     t0 = time.perf_counter()
     try:
-        for order in orders:
-            net = WarmStartNet(in_ch=in_channels(order), width=width, out_ch=2, n_layers=n_layers, ksize=ksize,
+        for name, order, lags, n_layers, ksize, width in specs:
+            net = WarmStartNet(in_ch=in_channels(lags), width=width, out_ch=2, n_layers=n_layers, ksize=ksize,
                                n=bie.N, max_batch=batch, seed=seed)
-            nets["network" if order == 3 else f"network{order}"] = (net, None)
-            scale = train(bie, net, mus, G, np.arange(order, 3 + n_train), epochs=epochs, batch=batch, lr=lr,
-                          seed=seed, order=order)
-            nets["network" if order == 3 else f"network{order}"] = (net, scale)
+            nets[name] = (net, None)
+            scale = train(bie, net, mus, G, np.arange(max(order, lags), 3 + n_train), epochs=epochs, batch=batch,
+                          lr=lr, seed=seed, order=order, lags=lags)
+            nets[name] = (net, scale)
     except Exception:
         for net, _ in nets.values():
             net.close()
@@ -223,7 +232,7 @@ def _train_nets(bie, mus, G, n_train, orders, epochs, batch, lr, seed, width, n_
 
 
 def experiment(alpha, n_panels=256, n_train=2000, n_test=200, dt=1e-3, tol=1e-11, epochs=40, batch=16,
-               lr=1e-3, seed=5, width=64, n_layers=4, ksize=9, orders=(3,)):
+               lr=1e-3, seed=5, width=64, n_layers=4, ksize=9, specs=None):
     """Plain solves for n_train + n_test + 3 steps of a star with moving exterior forcing, network
     training on the first n_train, iterations and times from each initial guess on the rest."""
     rng = np.random.default_rng(seed)
@@ -236,8 +245,9 @@ def experiment(alpha, n_panels=256, n_train=2000, n_test=200, dt=1e-3, tol=1e-11
         G = boundary_data(bie, forcing, times)
         mus, its = plain_solves(bie, G, tol)
         t_plain = time.perf_counter() - t0
-        nets, t_train, scale = _train_nets(bie, mus, G, n_train, orders, epochs, batch, lr, seed, width, n_layers,
-                                           ksize)
+        if specs is None:
+            specs = (("network", 3, 3, n_layers, ksize, width),)
+        nets, t_train, scale = _train_nets(bie, mus, G, n_train, specs, epochs, batch, lr, seed)
         try:
             test_idx = np.arange(3 + n_train, steps)
             ev = evaluate(bie, nets, mus, G, test_idx, tol)
@@ -291,7 +301,7 @@ class StepProblem:
 
 
 def step_experiment(wl, n_panels=256, n_train=2000, n_test=200, tol=1e-11, precision=VP_PREC_FP64, epochs=40,
-                    batch=16, lr=1e-3, seed=5, width=64, n_layers=4, ksize=9, log=None, orders=(3, 4)):
+                    batch=16, lr=1e-3, seed=5, width=64, n_layers=4, ksize=9, log=None, specs=STEP_SPECS):
     """Steps of the coupled problem: plain solves for n_train + n_test + 3 steps, network training on
     the first n_train, then per held-out step the volume potential, its boundary trace and GMRES from
     each initial guess (step time = volume part + guess + GMRES)."""
@@ -316,8 +326,9 @@ def step_experiment(wl, n_panels=256, n_train=2000, n_test=200, tol=1e-11, preci
         t_plain = time.perf_counter() - t0
         if log:
             log(f"plain solves: mean {np.mean(its):.1f} iterations, {t_plain:.1f} s")
-        nets, t_train, scale = _train_nets(bie, mus, G, n_train, orders, epochs, batch, lr, seed, width, n_layers,
-                                           ksize)
+        if specs is None:
+            specs = (("network", 3, 3, n_layers, ksize, width),)
+        nets, t_train, scale = _train_nets(bie, mus, G, n_train, specs, epochs, batch, lr, seed)
         try:
             if log:
                 log(f"training: {t_train:.1f} s, loss {scale['losses'][0]:.3e} -> {np.mean(scale['losses'][-20:]):.3e}")
