@@ -6,7 +6,7 @@ import paper_1908_07392_gb300 as V
 from paper_1908_07392_gb300 import inputs as I
 
 TOL_FP64 = 1e-10   # relative max-norm error per field (u, du/dx, du/dy), plain FP64
-TOL_SPLIT = 1e-9   # the same for the split-precision (sliced fp16 tensor-core) form
+TOL_SPLIT = 1e-9   # the same for the split-precision (sliced bf16 tensor-core) form
 
 
 def gpu_eval(w, order=40, precision=V.VP_PREC_FP64, levels=None):

@@ -1,4 +1,4 @@
-"""Split-precision form (sliced fp16 operands on the tensor cores) against the FP64 oracle and FP64 path."""
+"""Split-precision form (sliced bf16 operands on the tensor cores) against the FP64 oracle and FP64 path."""
 import numpy as np
 import pytest
 
