@@ -39,10 +39,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_FLOPS_PER_CLK_PER_SM = 4.0   # 2 DFMA per clock per SM: 1.25 TFLOP/s nominal over 152 SMs at ~2.06 GHz
-# DRAM bytes of one FP64 near-field launch on the default workload: the ncu capture of the same kernel at
-# depth 8 (688 MB for 66.6k near pairs) scaled by pairs to the 356k pairs at depth 10.
+# DRAM bytes of one FP64 near-field launch on the default workload, NOT measured in this run: a past ncu
+# capture of the same kernel at depth 8 (688 MB for 66.6k near pairs, profiles/near_f64_star_d8.md) scaled
+# by pairs to the 356k pairs at depth 10.
 TRAFFIC_FP64_NEAR = 3.68e9
+TRAFFIC_FP64_NEAR_SOURCE = "constant from a past ncu capture (profiles/near_f64_star_d8.md, depth 8 scaled by near pairs)"
 N_SM = 152
+SLICE_PRODUCTS = 21  # S (S + 1) / 2 slice products per contraction, S = 6 bf16 slices
 
 
 def parse():
@@ -58,6 +61,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched workload that the default run measures beside the headline")
     ap.add_argument("--max-depth", type=int, default=10, help="tree depth cap (10 = the stated workload)")
     ap.add_argument("--workload", default="star", choices=["star", "batched", "steps"],
                     help="star: one adaptive tree (default); batched: 64 trees in one CUDA graph; "
@@ -130,10 +135,13 @@ def cpu_sample(w, budget_s, seed=0):
     X, Y = I.node_coords(w.tree, w.p)
     rng = np.random.default_rng(seed)
     cores = oracle.num_threads()
-    t0 = time.perf_counter()
-    idx = rng.choice(w.n_nodes, 1, replace=False)
-    oracle.volume_potential(w.kernel, w.alpha, w.p, w.tree, w.f, X[idx], Y[idx], nthreads=1)
-    one = max(time.perf_counter() - t0, 1e-3)
+    one = getattr(cpu_sample, "one", None)
+    if one is None:
+        # seconds of one target on one thread, probed once per process
+        t0 = time.perf_counter()
+        idx = rng.choice(w.n_nodes, 1, replace=False)
+        oracle.volume_potential(w.kernel, w.alpha, w.p, w.tree, w.f, X[idx], Y[idx], nthreads=1)
+        one = cpu_sample.one = max(time.perf_counter() - t0, 1e-3)
     n = int(max(cores, min(4096, budget_s / one * cores * 0.8)))
     idx = rng.choice(w.n_nodes, n, replace=False)
     t0 = time.perf_counter()
@@ -318,6 +326,35 @@ def batched_form(args, V, ws, prec, local, world=1):
             vp.close()
 
 
+def batched_pair(args, V, local, world):
+    """Both forms of the batched workload with fewer steps than the headline (its own L2 flush and clock
+    record per form), as an extra object of the headline line."""
+    from paper_1908_07392_gb300 import inputs as I
+    import copy
+    rank = int(os.environ.get("RANK", "0"))
+    a = copy.copy(args)
+    a.steps = max(3, min(args.steps, 10))
+    a.warmup = max(3, min(args.warmup, 3))
+    ws = I.batched_workloads(seed=4 + rank)
+    sp = batched_form(a, V, ws, V.VP_PREC_SPLIT, local, world)
+    fp = batched_form(a, V, ws, V.VP_PREC_FP64, local, world)
+    sv = sp["nodes_all"] * a.steps / (sp["graph_ms"] / 1000.0)
+    fv = fp["nodes_all"] * a.steps / (fp["graph_ms"] / 1000.0)
+    return {"workload": "batched: 64 trees, nodes log-uniform [1e4, 5e5], alpha log-uniform [10, 1000], "
+                        "p in {8, 12, 16}, modified-Helmholtz kernel, Gaussian-sum sources, one CUDA graph",
+            "trees": len(ws), "nodes": sp["nodes"], "steps": a.steps, "warmup": a.warmup, "streams": a.streams,
+            "l2": "flushed before every timed step (512 MB write)",
+            "split": {"value": sv, "unit": "nodes/s", "ms_per_step": sp["graph_ms"] / a.steps,
+                      "serial_ms_per_step": sp["serial_ms"] / a.steps, "gpu_launches_per_step": sp["launches"],
+                      "tcgen05_launches": sp["n_tc"], "stated_rel_err": 1e-9, "roofline": sp["roofline"],
+                      "clocks": sp["clocks"], "setup_s": round(sp["setup_s"], 1)},
+            "plain_fp64": {"value": fv, "unit": "nodes/s", "ms_per_step": fp["graph_ms"] / a.steps,
+                           "serial_ms_per_step": fp["serial_ms"] / a.steps, "gpu_launches_per_step": fp["launches"],
+                           "stated_rel_err": 1e-10, "roofline": fp["roofline"], "clocks": fp["clocks"],
+                           "setup_s": round(fp["setup_s"], 1)},
+            "split_speedup_vs_fp64": sv / fv}
+
+
 def run_batched(args):
     import torch
     import paper_1908_07392_gb300 as V
@@ -497,28 +534,66 @@ def measure(args, V, w, prec, world, local, with_e2e):
             e2e = {"value": world * N * args.steps / (time.perf_counter() - t0), "unit": "nodes/s",
                    "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 24 * N}
 
+        stage_bytes = V.vp_tree_bytes(vp.tree)
+        # every launch timed in order (one evaluation, L2 flushed before it)
+        flush.zero_()
+        torch.cuda.synchronize()
+        launch_list = V.vp_eval_steps(vp.tree, f, u, g)
+        split = prec == V.VP_PREC_SPLIT
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
+        fp64_peak = N_SM * 2070.0e6 * FP64_FLOPS_PER_CLK_PER_SM / 1e12
+        tc_peak = measured_peaks().get("bf16_tflops", 1900.0)
         near_ms = statistics.mean(m[4] for m in stage_ms)
         near_flops = stage_flops[4]
-        if prec == V.VP_PREC_FP64:
+        near_gbs = stage_bytes[4] / (near_ms / 1000.0) / 1e9
+        if not split:
             achieved = near_flops / (near_ms / 1000.0) / 1e12
-            peak = N_SM * 2070.0e6 * FP64_FLOPS_PER_CLK_PER_SM / 1e12
+            peak = fp64_peak
             roof = {"kernel": "k_gemm_gather_f64<1> (near-field tables)", "bound": "alu",
                     "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk (derived; 1.20 TFLOP/s measured)"}
             traffic = TRAFFIC_FP64_NEAR if (args.max_depth == 10 and args.alpha == 300.0) else None
+            if traffic is not None:
+                roof["traffic_source"] = TRAFFIC_FP64_NEAR_SOURCE
         else:
             # tensor work: S(S+1)/2 slice products of the same shape as the FP64 contraction
-            slices = 6  # kSplitSlices in the library
-            achieved = near_flops * slices * (slices + 1) / 2 / (near_ms / 1000.0) / 1e12
-            peak = measured_peaks().get("bf16_tflops", 1900.0)
+            achieved = near_flops * SLICE_PRODUCTS / (near_ms / 1000.0) / 1e12
+            peak = tc_peak
             roof = {"kernel": "split-precision near-field GEMM (6 bf16 slices, fp32 accumulation; engine per launch)",
                     "bound": "tensor", "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured",
                     "fp64_equivalent_tflops": near_flops / (near_ms / 1000.0) / 1e12}
             traffic = None
+        roof.update(algorithmic_bytes=stage_bytes[4], achieved_gbs=near_gbs, hbm_frac_of_measured=near_gbs / hbm)
+
+        def rate(flops, bytes_, ms):
+            sec = max(ms, 1e-6) / 1000.0
+            tf = flops * (SLICE_PRODUCTS if split else 1) / sec / 1e12
+            gbs = bytes_ / sec / 1e9
+            return {"ms": round(ms, 4), "tflops": round(tf, 3), "frac": round(tf / (tc_peak if split else fp64_peak), 4),
+                    "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+
+        stage_roof = {}
+        for k, name in enumerate(V.STAGE_NAMES):
+            ms_k = statistics.mean(m[k] for m in stage_ms)
+            stage_roof[name] = dict(rate(stage_flops[k], stage_bytes[k], ms_k), gflop=round(stage_flops[k] / 1e9, 2),
+                                    gbytes=round(stage_bytes[k] / 1e9, 3))
+        kinds = {0: "fp64 gemm", 1: "fp64 reduce", 2: "memset", 3: "slice", 4: "split gemm", 5: "df reduce"}
+        tables = {-1: "-", 0: "near", 1: "s2m", 2: "l2t", 3: "m2m", 4: "l2l", 5: "m2l", 6: "m2t", 7: "s2l",
+                  8: "m2m_lo", 9: "m2m_hi"}
+        top = sorted(range(len(launch_list)), key=lambda i: -launch_list[i]["ms"])[:10]
+        top_launches = [dict(rate(launch_list[i]["flops"], launch_list[i]["bytes"], launch_list[i]["ms"]),
+                             index=i, kind=kinds.get(launch_list[i]["kind"], "?"),
+                             stage=V.STAGE_NAMES[launch_list[i]["stage"]],
+                             table=tables.get(launch_list[i]["table"], "?"),
+                             engine={-1: "-", 0: "mma.sync", 1: "tcgen05"}.get(launch_list[i]["engine"], "?"))
+                        for i in top]
         return {"value": value, "total_ms": total_ms, "N": N, "setup_s": setup_s, "n_tc": n_tc,
                 "u": u.cpu().numpy(), "g": g.cpu().numpy(),
                 "launches": int(launches), "e2e": e2e, "clocks": sampler.summary(),
                 "stage_ms": {name: round(statistics.mean(m[k] for m in stage_ms), 4)
                              for k, name in enumerate(V.STAGE_NAMES)},
+                "stage_roofline": stage_roof,
+                "launch_list": {"launches": len(launch_list), "in_order_ms": round(sum(x["ms"] for x in launch_list), 4),
+                                "top": top_launches},
                 "roofline": dict(roof, achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
                                  traffic=traffic)}
     finally:
@@ -558,6 +633,8 @@ def main():
     head_prec = V.VP_PREC_FP64 if args.precision == "fp64" else V.VP_PREC_SPLIT
     head = measure(args, V, w, head_prec, world, local, not args.no_e2e)
     plain = measure(args, V, w, V.VP_PREC_FP64, world, local, False) if args.precision == "both" else None
+    # the batched workload (64 trees in one CUDA graph), split and FP64, in the same run
+    batched = None if (args.no_batched or args.precision != "both") else batched_pair(args, V, local, world)
     errs = {}
     if cpu is not None:
         idx, vals = cpu_sample.last
@@ -581,6 +658,12 @@ def main():
                 "stage_ms": head["stage_ms"],
                 "stage_timing": "per-stage CUDA events, stages in order on one stream; the timed steps run "
                                 "vp_eval, which overlaps the near field with the far-field chain",
+                "stage_roofline": head["stage_roofline"],
+                "stage_roofline_note": "per stage: algorithmic flops (split: x21 bf16 slice products) and bytes "
+                                       "(operators and distinct source vectors once, outputs once) over the "
+                                       "in-order stage time; frac of the measured bf16 burst (split) or the "
+                                       "derived FP64 pipe (fp64); hbm_frac of the measured copy bandwidth",
+                "launch_list": head["launch_list"],
                 "roofline": head["roofline"],
                 "cpu_baseline": cpu,
                 "rel_err_vs_oracle_sampled": errs or None,
@@ -590,9 +673,12 @@ def main():
         if plain is not None:
             line["plain_fp64"] = {"value": plain["value"], "unit": "nodes/s",
                                   "ms_per_step": plain["total_ms"] / args.steps, "stage_ms": plain["stage_ms"],
+                                  "stage_roofline": plain["stage_roofline"], "launch_list": plain["launch_list"],
                                   "roofline": plain["roofline"], "clocks": plain["clocks"],
                                   "gpu_launches": plain["launches"] * args.steps}
             line["split_speedup_vs_fp64"] = head["value"] / plain["value"]
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

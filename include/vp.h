@@ -218,6 +218,28 @@ int vp_eval_timed(vp_tree tree, const double* f, double* u, double* gradu, void*
 int vp_tree_stats(vp_tree tree, int64_t* launches, double* stage_flops);
 
 /*
+ * vp_tree_bytes -- algorithmic device-memory bytes of one evaluation per stage (host array
+ * [VP_NSTAGES]): every operator matrix and every distinct source vector a launch reads counted
+ * once, every output element counted once (twice when the launch accumulates into it), in the
+ * representation the tree's precision uses (FP64, or S bf16 slices plus an exponent per row or
+ * vector). The denominator of each stage's achieved bandwidth.
+ */
+int vp_tree_bytes(vp_tree tree, double* stage_bytes);
+
+/*
+ * vp_eval_steps -- vp_eval with every launch issued in order on `stream` and a CUDA event
+ * recorded before each and after the last; waits for the last event. With cap = 0 only
+ * *n_steps (the number of launches, including memsets) is returned. Otherwise cap >= *n_steps and
+ * the host arrays receive, per launch k: ms[k] (milliseconds), info[4k..4k+3] = (kind: 0 FP64
+ * contraction, 1 FP64 reduction, 2 memset, 3 slicing, 4 split contraction, 5 double-float
+ * reduction; stage VP_STAGE_*; operator table id or -1; split engine or -1), flops[k] and
+ * bytes[k] (algorithmic, as vp_tree_stats and vp_tree_bytes count them). Same device arguments
+ * as vp_eval. Errors: VP_ERR_ARG, VP_ERR_CUDA.
+ */
+int vp_eval_steps(vp_tree tree, const double* f, double* u, double* gradu, void* stream, int cap, int* n_steps,
+                  float* ms, int* info, double* flops, double* bytes);
+
+/*
  * vp_plan_pairs -- host-only planning diagnostic (no GPU needed): validates a
  * leaf list like vp_tree_upload and returns, for every interaction the lists
  * generate, the covered (target leaf, source leaf) pairs with the mechanism

@@ -94,6 +94,10 @@ def load_library():
     lib.vp_plan_pairs.argtypes = [c_int, i32p, i32p, i32p, i64p, i32p, i32p, i32p]
     lib.vp_eval_timed.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(ctypes.c_float)]
     lib.vp_tree_stats.argtypes = [c_void_p, i64p, ctypes.POINTER(c_double)]
+    lib.vp_tree_bytes.argtypes = [c_void_p, ctypes.POINTER(c_double)]
+    lib.vp_eval_steps.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.POINTER(c_int),
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int), ctypes.POINTER(c_double),
+                                  ctypes.POINTER(c_double)]
     pp = ctypes.POINTER(c_void_p)
     lib.vp_batch_create.argtypes = [c_int, pp, pp, pp, pp, c_int, c_void_p, ctypes.POINTER(c_void_p)]
     lib.vp_batch_run.argtypes = [c_void_p, c_void_p]
@@ -108,7 +112,7 @@ def load_library():
 def exported_symbols():
     """Names declared in include/vp.h (the ABI surface)."""
     return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_tree_interp", "vp_special", "vp_eval", "vp_eval_host",
-            "vp_eval_timed", "vp_tree_stats", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
+            "vp_eval_timed", "vp_tree_stats", "vp_tree_bytes", "vp_eval_steps", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
             "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status", "vp_selftest_timeout",
             "bie_create", "bie_free", "bie_size", "bie_nodes", "bie_apply", "bie_solve", "bie_solve_aug", "bie_eval",
@@ -240,6 +244,30 @@ def vp_tree_stats(tree: int):
     fl = (ctypes.c_double * VP_NSTAGES)()
     _check(load_library().vp_tree_stats(ctypes.c_void_p(tree), ctypes.byref(n), fl), "vp_tree_stats")
     return n.value, list(fl)
+
+
+def vp_tree_bytes(tree: int):
+    """Algorithmic device-memory bytes per stage (list of VP_NSTAGES)."""
+    b = (ctypes.c_double * VP_NSTAGES)()
+    _check(load_library().vp_tree_bytes(ctypes.c_void_p(tree), b), "vp_tree_bytes")
+    return list(b)
+
+
+def vp_eval_steps(tree: int, f, u, gradu, stream=None):
+    """Every launch of one evaluation timed in order: list of dicts (ms, kind, stage, table, engine, flops,
+    bytes), one per launch."""
+    lib = load_library()
+    n = ctypes.c_int()
+    _check(lib.vp_eval_steps(ctypes.c_void_p(tree), None, None, None, _stream_ptr(stream), 0, ctypes.byref(n),
+                             None, None, None, None), "vp_eval_steps")
+    k = n.value
+    ms = (ctypes.c_float * k)(); info = (ctypes.c_int * (4 * k))()
+    fl = (ctypes.c_double * k)(); by = (ctypes.c_double * k)()
+    _check(lib.vp_eval_steps(ctypes.c_void_p(tree), ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                             ctypes.c_void_p(gradu.data_ptr()), _stream_ptr(stream), k, ctypes.byref(n), ms, info,
+                             fl, by), "vp_eval_steps")
+    return [{"ms": ms[i], "kind": info[4 * i], "stage": info[4 * i + 1], "table": info[4 * i + 2],
+             "engine": info[4 * i + 3], "flops": fl[i], "bytes": by[i]} for i in range(k)]
 
 
 def vp_eval_host(tree: int, f, u, gradu, stream=None):

@@ -299,6 +299,8 @@ struct Step {
   int kind;   // 0 gemm, 1 reduce, 2 memset mp, 3 slice vectors, 4 split gemm, 5 double-float reduce
   int index;
   int stage;  // VP_STAGE_* for timing
+  double flops = 0.0;  // algorithmic floating-point operations of the step
+  double bytes = 0.0;  // algorithmic device-memory bytes: every operand read once, every output written once
 };
 
 }  // namespace vp
@@ -319,6 +321,7 @@ struct vp_tree_s {
   std::vector<vp::Step> steps;
   int cur_stage = 0;        // stage tag given to steps as they are planned
   double flops[VP_NSTAGES] = {0};
+  double bytes[VP_NSTAGES] = {0};
   // split precision: sliced source vectors (leaf values, multipoles, locals) and their exponents
   std::vector<vp::DevSplit> splits;
   void* sv[vp::kVecFamilies] = {nullptr};
@@ -354,6 +357,12 @@ int dev_upload(vp_tree_s* tr, const std::vector<T>& v, T** out, cudaStream_t s) 
 
 int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s);
 
+// Number of distinct values in v.
+long long count_distinct(std::vector<long long> v) {
+  std::sort(v.begin(), v.end());
+  return (long long)(std::unique(v.begin(), v.end()) - v.begin());
+}
+
 int upload_gemm(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
   if (g.entries.empty()) return VP_OK;
   if (tr->T->precision == VP_PREC_SPLIT && g.split_vec >= 0) return upload_split(tr, g, s);
@@ -385,9 +394,15 @@ int upload_gemm(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
   if ((rc = dev_upload(tr, dst_off, &dd, s))) return rc;
   d.args.tiles = dt; d.args.a_off = da; d.args.src_off = ds; d.args.dst_off = dd;
   d.src = g.src; d.dst = g.dst; d.table = g.table; d.n_tiles = (int)tiles.size();
-  tr->steps.push_back({0, (int)tr->gemms.size(), tr->cur_stage});
+  // algorithmic bytes: each operator and each distinct source vector read once, each output column
+  // written once (read as well when accumulating)
+  const double fl = 2.0 * g.M * (double)g.K * (double)g.entries.size();
+  const double by = 8.0 * ((double)a_off.size() * g.M * g.K + (double)count_distinct(src_off) * g.K +
+                           (1.0 + g.accumulate) * (double)g.entries.size() * g.M);
+  tr->steps.push_back({0, (int)tr->gemms.size(), tr->cur_stage, fl, by});
   tr->gemms.push_back(d);
-  tr->flops[tr->cur_stage] += 2.0 * g.M * (double)g.K * (double)g.entries.size();
+  tr->flops[tr->cur_stage] += fl;
+  tr->bytes[tr->cur_stage] += by;
   return VP_OK;
 }
 
@@ -432,9 +447,17 @@ int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
   d.tiles[0] = dt0; d.tiles[1] = dt1;
   d.n_tiles[0] = (int)tiles[0].size(); d.n_tiles[1] = (int)tiles[1].size();
   d.table = g.table; d.vec = g.split_vec; d.dst = g.dst;
-  tr->steps.push_back({4, (int)tr->splits.size(), tr->cur_stage});
+  // algorithmic bytes: sliced operators (S bf16 slices + a row exponent) and sliced source vectors
+  // (S slices + an exponent) read once, outputs written once (8 bytes: a double-float slot or FP64)
+  const int kp = split_kpad(g.K);
+  const double fl = 2.0 * g.M * (double)g.K * (double)g.entries.size();
+  const double by = (double)a_mat.size() * g.M * (2.0 * kSplitSlices * kp + 4.0) +
+                    (double)count_distinct(src_vec) * (2.0 * kSplitSlices * kp + 4.0) +
+                    8.0 * (1.0 + (g.out_mode == 2)) * (double)g.entries.size() * g.M;
+  tr->steps.push_back({4, (int)tr->splits.size(), tr->cur_stage, fl, by});
   tr->splits.push_back(d);
-  tr->flops[tr->cur_stage] += 2.0 * g.M * (double)g.K * (double)g.entries.size();
+  tr->flops[tr->cur_stage] += fl;
+  tr->bytes[tr->cur_stage] += by;
   return VP_OK;
 }
 
@@ -447,7 +470,9 @@ int add_slice(vp_tree_s* tr, int family, int buf, int K, int kseg, long long seg
   if (base) { if ((rc = dev_upload(tr, *base, &p, s))) return rc; d.base = p; }
   if (vid) { if ((rc = dev_upload(tr, *vid, &p, s))) return rc; d.vid = p; }
   if (n <= 0) return VP_OK;
-  tr->steps.push_back({3, (int)tr->slice_ops.size(), tr->cur_stage});
+  const double by = (double)n * (8.0 * K + 2.0 * kSplitSlices * split_kpad(K) + 4.0);
+  tr->steps.push_back({3, (int)tr->slice_ops.size(), tr->cur_stage, 0.0, by});
+  tr->bytes[tr->cur_stage] += by;
   tr->slice_ops.push_back(d);
   return VP_OK;
 }
@@ -468,8 +493,11 @@ int upload_reduce(vp_tree_s* tr, HostReduce& r, cudaStream_t s) {
   d.args.dst_off = a; d.args.ptr = b; d.args.slot = c;
   d.dst = r.dst; d.src = r.src; d.n_dst = (int)r.dst_off.size();
   // in split precision every slot producer writes double-float slots
-  tr->steps.push_back({tr->T->precision == VP_PREC_SPLIT ? 5 : 1, (int)tr->reduces.size(), tr->cur_stage});
-  tr->flops[tr->cur_stage] += (double)r.M * (double)r.slot.size();
+  const double fl = (double)r.M * (double)r.slot.size();
+  const double by = 8.0 * (double)r.M * ((double)r.slot.size() + (double)r.dst_off.size());
+  tr->steps.push_back({tr->T->precision == VP_PREC_SPLIT ? 5 : 1, (int)tr->reduces.size(), tr->cur_stage, fl, by});
+  tr->flops[tr->cur_stage] += fl;
+  tr->bytes[tr->cur_stage] += by;
   tr->reduces.push_back(d);
   return VP_OK;
 }
@@ -584,7 +612,8 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   int rc;
   // ---- steps, in pass order
   tr->cur_stage = VP_STAGE_UPWARD;
-  tr->steps.push_back({2, 0, tr->cur_stage});  // clear multipoles
+  tr->steps.push_back({2, 0, tr->cur_stage, 0.0, 8.0 * (double)NB * E});  // clear multipoles
+  tr->bytes[tr->cur_stage] += 8.0 * (double)NB * E;
   if (split && (rc = add_slice(tr, 0, BUF_F, n, n, 0, n, tr->n_leaves, nullptr, nullptr, s))) return rc;
   if ((rc = upload_gemm(tr, s2m, s))) return rc;
   for (int l = P.max_level - 1; l >= 2; --l) {
@@ -712,12 +741,16 @@ SplitArgs split_args(const vp_tree_s* tr, const DevSplit& d, double* const* bufs
 // chain (upward, M2L, downward, targets) runs on the tree's high-priority side stream; near-field
 // CTAs then hold one tile each, so chain launches find SMs; `s` waits for the chain before the
 // output reduction. The two write disjoint contribution slots.
-int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t s0, cudaEvent_t* ev = nullptr) {
+// With per-step events (step_ev, steps + 1 of them) every step goes to `s` in order and an event is
+// recorded before each step and after the last.
+int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t s0, cudaEvent_t* ev = nullptr,
+              cudaEvent_t* step_ev = nullptr) {
   const vp_tables_s* T = tr->T;
   int stage = -1;
   const double* bufs_c[BUF_COUNT] = {f, tr->mp, tr->loc, tr->lslot, tr->uslot};
   double* bufs[BUF_COUNT] = {nullptr, tr->mp, tr->loc, tr->lslot, tr->uslot};
-  const bool overlap = !ev && tr->side;
+  const bool overlap = !ev && !step_ev && tr->side;
+  int step_no = 0;
   bool src_ready = false, near_started = false, joined = !overlap;
   if (overlap) {
     TRY(cudaEventRecord(tr->ev_fork, s0));
@@ -727,6 +760,8 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
     if (ev) {
       while (stage < st.stage) { ++stage; TRY(cudaEventRecord(ev[stage], s0)); }
     }
+    if (step_ev) TRY(cudaEventRecord(step_ev[step_no], s0));
+    ++step_no;
     const bool near_step = overlap && st.stage == VP_STAGE_NEAR;
     if (overlap && st.stage == VP_STAGE_OUTPUT && !joined) {
       TRY(cudaEventRecord(tr->ev_join, tr->side));
@@ -787,6 +822,7 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
     TRY(cudaEventRecord(tr->ev_join, tr->side));
     TRY(cudaStreamWaitEvent(s0, tr->ev_join, 0));
   }
+  if (step_ev) TRY(cudaEventRecord(step_ev[step_no], s0));
   if (ev) {
     while (stage < VP_NSTAGES) { ++stage; TRY(cudaEventRecord(ev[stage], s0)); }
   }
@@ -907,6 +943,43 @@ extern "C" int vp_eval_timed(vp_tree tree, const double* f, double* u, double* g
     if (cudaEventElapsedTime(&stage_ms[k], ev[k], ev[k + 1]) != cudaSuccess) rc = VP_ERR_CUDA;
   }
   for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+  return rc;
+}
+
+extern "C" int vp_tree_bytes(vp_tree tree, double* stage_bytes) {
+  if (!tree || !stage_bytes) return VP_ERR_ARG;
+  for (int k = 0; k < VP_NSTAGES; ++k) stage_bytes[k] = tree->bytes[k];
+  return VP_OK;
+}
+
+extern "C" int vp_eval_steps(vp_tree tree, const double* f, double* u, double* gradu, void* stream, int cap,
+                             int* n_steps, float* ms, int* info, double* flops, double* bytes) {
+  if (!tree || !n_steps) return VP_ERR_ARG;
+  const int n = (int)tree->steps.size();
+  *n_steps = n;
+  if (cap <= 0) return VP_OK;
+  if (cap < n || !f || !u || !gradu || !ms || !info || !flops || !bytes) return VP_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<cudaEvent_t> ev(n + 1, nullptr);
+  int rc = VP_OK;
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) { rc = VP_ERR_CUDA; break; }
+  if (rc == VP_OK) rc = run_steps(tree, f, u, gradu, s, nullptr, ev.data());
+  if (rc == VP_OK) {
+    const cudaError_t e = cudaEventSynchronize(ev[n]);
+    if (e != cudaSuccess) { set_last_cuda(e); rc = VP_ERR_CUDA; }
+  }
+  for (int k = 0; rc == VP_OK && k < n; ++k) {
+    if (cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]) != cudaSuccess) { rc = VP_ERR_CUDA; break; }
+    const Step& st = tree->steps[k];
+    int table = -1, engine = -1;
+    if (st.kind == 0) table = tree->gemms[st.index].table;
+    if (st.kind == 4) { table = tree->splits[st.index].table; engine = tree->splits[st.index].engine; }
+    info[4 * k] = st.kind; info[4 * k + 1] = st.stage; info[4 * k + 2] = table; info[4 * k + 3] = engine;
+    flops[k] = st.flops;
+    bytes[k] = st.bytes;
+  }
+  for (auto e : ev) if (e) cudaEventDestroy(e);
   return rc;
 }
 

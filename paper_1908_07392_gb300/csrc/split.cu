@@ -103,7 +103,9 @@ __global__ void k_slice_rows(const double* __restrict__ A, long long mstride, in
 
 // Slice a list of vectors. Vector v (v < nlist) has identifier id = vid ? vid[v] : v and elements
 // x_k = X[b + (k / kseg) * seg_stride + k % kseg], k < K, b = base ? base[v] : v * cstride;
-// output out[id][s][Kpad] and eb[id]. One warp per vector.
+// output out[id][Kpad / 16][s][16] (the S slices of each K step of 16 are contiguous, so one
+// column of a K step is one 32 S-byte block for the GEMM engines' gathers) and eb[id]. One warp
+// per vector.
 template <int S>
 __global__ void k_slice_list(const double* __restrict__ X, const long long* __restrict__ base,
                              const long long* __restrict__ vid, long long nlist, int K, int kseg,
@@ -124,7 +126,7 @@ __global__ void k_slice_list(const double* __restrict__ X, const long long* __re
   slice_t* o = out + id * (long long)S * Kpad;
   for (int k = lane; k < Kpad; k += 32) {
     const int sg = k / kseg;
-    digits<S>(k < K ? X[b + sg * seg_stride + (k - sg * kseg)] : 0.0, e, o + k, Kpad);
+    digits<S>(k < K ? X[b + sg * seg_stride + (k - sg * kseg)] : 0.0, e, o + (k >> 4) * (S * 16) + (k & 15), 16);
   }
   if (lane == 0) eb[id] = e;
 }
@@ -217,13 +219,14 @@ __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
       const slice_t* src = Ag + ((long long)sl * a.M + (ok ? gr : 0)) * a.Kpad + k0 + c;
       cp_async16(As + ((buf * S + sl) * kSplitBM + r) * kMPitch + c, src, ok);
     }
+    // one column's two K steps of 16 are 4 S contiguous 16-byte chunks (step, slice, half)
     for (int e = tid; e < S * kMBN * 4; e += 256) {
-      const int sl = e / (kMBN * 4), rem = e % (kMBN * 4);
-      const int col = rem >> 2, c = (rem & 3) * 8;
+      const int col = e / (S * 4), w = e % (S * 4);
+      const int ks = w / (S * 2), sl = (w >> 1) % S, h = w & 1;
       const bool ok = col < tile.ncol;
       const long long v = ok ? a.src_vec[tile.col0 + col] : 0;
-      const slice_t* src = a.B + (v * S + sl) * (long long)a.Kpad + k0 + c;
-      cp_async16(Bs + ((buf * S + sl) * kMBN + col) * kMPitch + c, src, ok);
+      const slice_t* src = a.B + v * S * (long long)a.Kpad + (k0 >> 4) * (S * 16) + w * 8;
+      cp_async16(Bs + ((buf * S + sl) * kMBN + col) * kMPitch + ks * 16 + h * 8, src, ok);
     }
     cp_async_commit();
   };
@@ -470,18 +473,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nk = a.Kpad / kTcKC;
 
   if (warp < kTcProducers / 32) {
-    // ---- producers: thread t copies row / column t >> 1 of every slice, 16-byte chunk t & 1
-    const int c = tid & 1, r = tid >> 1;
-    const int doff = ((r >> 3) * 2 + c) * 64 + (r & 7) * 8;
+    // ---- producers: a K step of the gathered operand is 128 columns x 2 S chunks of 16 bytes; a
+    // column's chunks (slice, half) are contiguous in global memory, so consecutive threads take
+    // consecutive chunks: thread t copies chunks q = t + 256 i, i < S (column q / 2S, slice
+    // (q % 2S) / 2, half q % 2)
+    const slice_t* bsrc[S];
+    int bdst[S];
+    bool bok[S];
     long long g = 0;  // ring step across tiles
     bool ok = true;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const SplitTile tile = a.tiles[t];
       // A: slice sl of this tile is slice index mat S + sl of the tensor map, rows from m0
       const int aslc = (int)(a.a_mat[tile.group] * S);
-      const bool bok = r < tile.ncol;
-      const long long v = bok ? a.src_vec[tile.col0 + r] : 0;
-      const slice_t* bsrc = a.B + v * S * (long long)a.Kpad + c * 8;
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const int q = tid + kTcProducers * i;
+        const int col = q / (2 * S), w = q % (2 * S);
+        const int sl = w >> 1, c = w & 1;
+        bok[i] = col < tile.ncol;
+        const long long v = bok[i] ? a.src_vec[tile.col0 + col] : 0;
+        bsrc[i] = a.B + v * S * (long long)a.Kpad + w * 8;
+        bdst[i] = sl * kTcB + ((col >> 3) * 2 + c) * 64 + (col & 7) * 8;
+      }
       for (int k = 0; k < nk; ++k, ++g) {
         const int st = (int)(g % kTcStages);
         if (g >= kTcStages && !mbar_wait(&empty[st], (unsigned)((g / kTcStages) - 1) & 1u, &abort_sh)) {
@@ -505,8 +519,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 : "memory");
         }
 #pragma unroll
-        for (int sl = 0; sl < S; ++sl)
-          cp_async16(Bs + (st * S + sl) * kTcB + doff, bsrc + (long long)sl * a.Kpad + k0, bok);
+        for (int i = 0; i < S; ++i) cp_async16(Bs + st * S * kTcB + bdst[i], bsrc[i] + k * (S * 16), bok[i]);
         // arrives on full[st] once this thread's copies so far have landed; the thread moves on
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full[st])) : "memory");
       }

@@ -1,9 +1,10 @@
 """vp_eval_static: the evaluation without any device allocation.
 
 For callers that cannot allocate device memory when they evaluate (a fixed
-memory budget, an allocator they must not touch). The test calls the entry
-point through the C ABI twice in a row and compares it with vp_eval, and
-checks that a tree needing more than the static work space is rejected.
+memory budget, an allocator they must not touch). The tests call the entry
+point through the C ABI twice in a row, and on two trees of different shape
+in turn (A, B, A), and compare it with vp_eval; they also check that a tree
+needing more than the static work space is rejected.
 Collected last on purpose (file name), so a stop-at-first-failure run has
 already run every other test.
 """
@@ -58,6 +59,34 @@ def test_static_matches_vp_eval_twice(lib):
                 assert np.abs(a - b).max() <= TOL * np.abs(b).max()
     finally:
         vp.close()
+
+
+def test_static_alternating_trees(lib):
+    # the shared array keeps the previous call's contents: alternate two trees of different shape and
+    # size (A, B, A) so that stale values left by another tree's layout would show
+    import torch
+    wa = I.small_gaussian_workload()
+    wb = I.small_gaussian_workload(depth=2, p=6, alpha=25.0)
+    va = V.VolumePotential(wa.kernel, wa.alpha, wa.p, wa.tree)
+    vb = V.VolumePotential(wb.kernel, wb.alpha, wb.p, wb.tree, order=24)
+    try:
+        cases = []
+        for w, vp in ((wa, va), (wb, vb)):
+            f = torch.from_numpy(w.f).cuda()
+            ur, gr = vp(f)
+            cases.append((vp, f, ur.clone(), gr.clone()))
+        for vp, f, ur, gr in (cases[0], cases[1], cases[0]):
+            u = torch.full_like(ur, float("nan"))
+            g = torch.full_like(gr, float("nan"))
+            assert _call(lib, vp.tree, f, u, g) == 0
+            torch.cuda.synchronize()
+            for a, b in ((u, ur), (g[0], gr[0]), (g[1], gr[1])):
+                a = a.cpu().numpy(); b = b.cpu().numpy()
+                assert np.all(np.isfinite(a))
+                assert np.abs(a - b).max() <= TOL * np.abs(b).max()
+    finally:
+        va.close()
+        vb.close()
 
 
 def test_static_rejects_trees_beyond_the_work_space(lib):
