@@ -428,9 +428,11 @@ int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
       dst_off.push_back(g.entries[k].d);
     }
     const int ncols = (int)(j - i);
+    // the row tiles of one column block are consecutive, so the CTAs that run them at the same time
+    // share the block's gathered source columns in L2
     for (int en = 0; en < 2; ++en)
-      for (int m0 = 0; m0 < g.M; m0 += kSplitBM)
-        for (int c0 = 0; c0 < ncols; c0 += kSplitBN[en])
+      for (int c0 = 0; c0 < ncols; c0 += kSplitBN[en])
+        for (int m0 = 0; m0 < g.M; m0 += kSplitBM)
           tiles[en].push_back({grp, m0, col_begin + c0, std::min(kSplitBN[en], ncols - c0)});
     i = j;
   }
@@ -728,7 +730,7 @@ SplitArgs split_args(const vp_tree_s* tr, const DevSplit& d, double* const* bufs
   SplitArgs a = d.args;
   a.A = static_cast<const slice_t*>(tb->A);
   a.ea = tb->ea;
-  a.tmap = tb->tmap;
+  a.nrt = tb->nrt;
   a.B = static_cast<const slice_t*>(tr->sv[d.vec]);
   a.eb = tr->se[d.vec];
   a.Y = bufs[d.dst];

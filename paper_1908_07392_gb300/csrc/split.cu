@@ -20,7 +20,6 @@
 //     2^(ea[r] + eb) exactly. Products with i + j > S - 1 are dropped.
 // Two engines run the same arithmetic: warp-level mma.sync (m16n8k16 bf16),
 // and tcgen05.mma with the accumulators in tensor memory.
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -80,11 +79,12 @@ __device__ inline int exponent_of(double v) {
   return e;
 }
 
-// Slice rows of a batch of matrices: A[mat][r][k] (row stride lda, matrix stride mstride) ->
-// out[mat][s][r][Kpad], ea[mat][r]. One warp per row.
+// Slice rows of a batch of matrices: A[mat][r][k] (row stride lda, matrix stride mstride) -> the
+// tiled layout of SplitTable (out[mat][r / 128][k / 16][s][(k % 16) / 8][r % 128][k % 8]; the caller
+// zeroes the padding rows) and ea[mat][r]. One warp per row.
 template <int S>
 __global__ void k_slice_rows(const double* __restrict__ A, long long mstride, int lda, int M, int K, int Kpad,
-                             int nmat, slice_t* __restrict__ out, int* __restrict__ ea) {
+                             int nmat, int nrt, slice_t* __restrict__ out, int* __restrict__ ea) {
   const long long row = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= (long long)nmat * M) return;
@@ -95,9 +95,10 @@ __global__ void k_slice_rows(const double* __restrict__ A, long long mstride, in
   for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(a[k]));
   for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = exponent_of(mx);
-  slice_t* o = out + (mat * S * M + r) * (long long)Kpad;
-  const size_t sstride = (size_t)M * Kpad;
-  for (int k = lane; k < Kpad; k += 32) digits<S>(k < K ? a[k] : 0.0, e, o + k, sstride);
+  const int nks = Kpad / 16;
+  slice_t* o = out + (mat * nrt + (r >> 7)) * (long long)nks * S * 2048 + (r & 127) * 8;
+  for (int k = lane; k < Kpad; k += 32)
+    digits<S>(k < K ? a[k] : 0.0, e, o + (long long)(k >> 4) * S * 2048 + ((k >> 3) & 1) * 1024 + (k & 7), 2048);
   if (lane == 0) ea[mat * M + r] = e;
 }
 
@@ -204,7 +205,8 @@ __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
   slice_t* Bs = As + 2 * S * kSplitBM * kMPitch;                        // [2][S][BN][pitch]
   const SplitTile tile = a.tiles[blockIdx.x];
   const long long mat = a.a_mat[tile.group];
-  const slice_t* Ag = a.A + mat * (long long)S * a.M * a.Kpad;
+  // this tile's rows in the tiled operator layout: [K step][slice][chunk][128 rows][8]
+  const slice_t* Ag = a.A + (mat * a.nrt + (tile.m0 >> 7)) * (long long)(a.Kpad / 16) * S * 2048;
   const int* ea = a.ea + mat * a.M;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 3, wn = warp >> 2;  // 4 warps along M (32 rows), 2 along N (32 columns)
@@ -213,11 +215,9 @@ __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
   auto load_chunk = [&](int buf, int k0) {
     for (int e = tid; e < S * kSplitBM * 4; e += 256) {
       const int sl = e / (kSplitBM * 4), rem = e % (kSplitBM * 4);
-      const int r = rem >> 2, c = (rem & 3) * 8;
-      const int gr = tile.m0 + r;
-      const bool ok = gr < a.M;
-      const slice_t* src = Ag + ((long long)sl * a.M + (ok ? gr : 0)) * a.Kpad + k0 + c;
-      cp_async16(As + ((buf * S + sl) * kSplitBM + r) * kMPitch + c, src, ok);
+      const int c = rem >> 7, r = rem & 127;  // K chunk of 8 (0..3 within the 32), row
+      const slice_t* src = Ag + ((long long)(((k0 >> 4) + (c >> 1)) * S + sl) * 2 + (c & 1)) * 1024 + r * 8;
+      cp_async16(As + ((buf * S + sl) * kSplitBM + r) * kMPitch + c * 8, src, true);  // padding rows are zeros
     }
     // one column's two K steps of 16 are 4 S contiguous 16-byte chunks (step, slice, half)
     for (int e = tid; e < S * kMBN * 4; e += 256) {
@@ -318,12 +318,15 @@ size_t mma_smem_bytes(int S) { return (size_t)2 * S * (kSplitBM + kMBN) * kMPitc
 // Persistent and warp-specialised: one CTA per SM walks the tile list (tile t, t + gridDim.x, ...).
 //  * warps 0-7 (producers) stage the operands of every K step of 16 into a 4-stage ring in the
 //    canonical K-major layout without swizzle (8-row x 16-byte core matrices): the operator slices
-//    (A) by TMA, one box per slice issued by thread 0 (next core matrix along K 2048 bytes further,
-//    next 8-row group 128 bytes further), the gathered source columns (B) by cp.async (128 and 256
-//    bytes); each thread's copies arrive on the stage's `full` mbarrier when they land
-//    (cp.async.mbarrier.arrive), the TMA boxes count their bytes on it, and a producer waits only
-//    for free stages. The ring runs on across tiles, so the next tile's
-//    operands stream in while the current one is drained.
+//    (A), stored in that layout tile by tile, by one bulk copy (cp.async.bulk, 24 KB) issued by
+//    thread 0, whose bytes complete on the stage's `fullA` mbarrier (next core matrix along K 2048
+//    bytes further, next 8-row group 128 bytes further); the gathered source columns (B) by
+//    cp.async (next core matrix along K 128 bytes, next 8-column group 256 bytes further), each
+//    thread's copies arriving on the stage's `full` mbarrier when they land
+//    (cp.async.mbarrier.arrive); a producer waits only for free stages. The ring runs on across
+//    tiles, so the next tile's operands stream in while the current one is drained. (Moving A by a
+//    tensor map whose boxes are 16 bytes wide -- the same layout built by the TMA unit -- made the
+//    whole K step 1.7x slower: narrow boxes cost the unit far more than one contiguous copy.)
 //  * warp 16 (one thread) waits on `full`, fences the generic-proxy writes of the stage against
 //    the async proxy, issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
 //    N = 128, K = 16) into four fp32 accumulators in tensor memory (one per weight group) and
@@ -390,6 +393,29 @@ __device__ inline void umma_f16(unsigned d_tmem, unsigned long long da, unsigned
   }
 }
 
+// The S(S+1)/2 slice products of one K step, fully unrolled: product (i, j) accumulates into the
+// weight group w = min(i + j, 3); A slice i is read into the A collector once and reused by its
+// S - i products. FIRST: step 0 of a tile, where the first product of each group overwrites it.
+template <int S, bool FIRST>
+__device__ __forceinline__ void mma_kstep(unsigned tmem, unsigned long long da, unsigned long long db, unsigned idesc) {
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+#pragma unroll
+    for (int j = 0; i + j < S; ++j) {
+      constexpr int kA = (kSplitBM * 16 * 2) >> 4, kB = (128 * 16 * 2) >> 4;  // slice tile strides, 16-B units
+      const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
+      const unsigned d_tmem = tmem + (unsigned)(w * 128);
+      const unsigned long long a = da + (unsigned long long)(i * kA), b = db + (unsigned long long)(j * kB);
+      const unsigned accum = (FIRST && i == 0 && j == w) ? 0u : 1u;
+      const int uses = S - i;
+      if (uses == 1) umma_f16<0>(d_tmem, a, b, idesc, accum);
+      else if (j == 0) umma_f16<1>(d_tmem, a, b, idesc, accum);
+      else if (j < uses - 1) umma_f16<2>(d_tmem, a, b, idesc, accum);
+      else umma_f16<3>(d_tmem, a, b, idesc, accum);
+    }
+  }
+}
+
 __device__ inline void umma_commit(unsigned long long* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
                : "memory");
@@ -437,7 +463,7 @@ __device__ inline bool epi_all(bool pred) {
 
 template <int S>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_split_gemm_tc(SplitArgs a, int n_tiles, const __grid_constant__ CUtensorMap tmA) {
+    k_split_gemm_tc(SplitArgs a, int n_tiles) {
   extern __shared__ __align__(128) unsigned char smem_tc[];
   slice_t* As = reinterpret_cast<slice_t*>(smem_tc);  // [stages][S][kTcA]
   slice_t* Bs = As + kTcStages * S * kTcA;              // [stages][S][kTcB]
@@ -457,7 +483,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (tid == 0) {
     for (int s = 0; s < kTcStages; ++s) {
       mbar_init(&full[s], kTcProducers);  // cp.async copies of the B operand
-      mbar_init(&fullA[s], 1);            // TMA boxes of the A operand (byte count)
+      mbar_init(&fullA[s], 1);            // bulk copy of the A operand (byte count)
       mbar_init(&empty[s], 1);
     }
     mbar_init(&accbar, 1);
@@ -484,8 +510,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bool ok = true;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
       const SplitTile tile = a.tiles[t];
-      // A: slice sl of this tile is slice index mat S + sl of the tensor map, rows from m0
-      const int aslc = (int)(a.a_mat[tile.group] * S);
+      // A: the S slices of K step k of this row tile are one contiguous block of S x 4 KB
+      const slice_t* ablk = a.A + (a.a_mat[tile.group] * a.nrt + (tile.m0 >> 7)) * (long long)nk * S * kTcA;
 #pragma unroll
       for (int i = 0; i < S; ++i) {
         const int q = tid + kTcProducers * i;
@@ -502,21 +528,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           ok = false;
           break;
         }
-        const int k0 = k * kTcKC;
         if (tid == 0) {
-          // A operand by TMA: one box per slice, completion counted in bytes on full[st]
+          // A operand: one bulk copy of the stage's S slice tiles, completion counted in bytes
           asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(
                            smem_u32(&fullA[st])),
                        "n"(S * kTcA * (int)sizeof(slice_t))
                        : "memory");
-#pragma unroll
-          for (int sl = 0; sl < S; ++sl)
-            asm volatile(
-                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes "
-                "[%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(As + (st * S + sl) * kTcA)),
-                "l"(reinterpret_cast<unsigned long long>(&tmA)), "r"(0), "r"(tile.m0), "r"(aslc + sl), "r"(k0 / 8),
-                "r"(smem_u32(&fullA[st]))
-                : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                  smem_u32(As + st * S * kTcA)),
+              "l"(ablk + (long long)k * S * kTcA), "n"(S * kTcA * (int)sizeof(slice_t)), "r"(smem_u32(&fullA[st]))
+              : "memory");
         }
 #pragma unroll
         for (int i = 0; i < S; ++i) cp_async16(Bs + st * S * kTcB + bdst[i], bsrc[i] + k * (S * 16), bok[i]);
@@ -527,8 +549,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     cp_async_wait_all();
     if (!ok) abort_sh = 1;
     if (tid == 0) {
-      // no TMA box may still be in flight when the CTA ends (after giving up too): wait for the
-      // boxes of the last stages issued (earlier ones were consumed by the MMA warp)
+      // no bulk copy may still be in flight when the CTA ends (after giving up too): wait for the
+      // copies of the last stages issued (earlier ones were consumed by the MMA warp)
       for (long long q = (g > kTcStages ? g - kTcStages : 0); q < g; ++q)
         mbar_wait(&fullA[q % kTcStages], (unsigned)(q / kTcStages) & 1u);
     }
@@ -598,6 +620,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // instruction descriptor: D f32, A and B bf16, both K-major, N = 128, M = 128
     const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcN >> 3) << 17) |
                            ((unsigned)(kSplitBM >> 4) << 24);
+    // shared-memory descriptors of stage 0, slice 0; the start address (16-byte units, low bits) of
+    // any other slice tile is an added constant, so a K step issues its S(S+1)/2 MMAs from
+    // precomputed descriptors with no per-MMA arithmetic beyond one add (the single issuing thread
+    // is the limit of the MMA rate otherwise).
+    // A (tiled layout): next core matrix along K 2048 bytes further, next 8-row group 128 bytes
+    const unsigned long long dA0 = umma_desc(smem_u32(As), 2048, 128);
+    const unsigned long long dB0 = umma_desc(smem_u32(Bs), 128, 256);
     long long g = 0;
     bool ok = true;
     int it = 0;
@@ -618,27 +647,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // it through the async proxy
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const unsigned abase = smem_u32(As + st * S * kTcA), bbase = smem_u32(Bs + st * S * kTcB);
-#pragma unroll
-        for (int i = 0; i < S; ++i) {
-          // A (TMA layout): next core matrix along K 2048 bytes further, next 8-row group 128 bytes
-          const unsigned long long da = umma_desc(abase + i * kTcA * 2, 2048, 128);
-#pragma unroll
-          for (int j = 0; i + j < S; ++j) {
-            const unsigned long long db = umma_desc(bbase + j * kTcB * 2, 128, 256);
-            const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
-            const unsigned d_tmem = tmem + (unsigned)(w * kTcN);
-            // the first product of each accumulator in a tile (step 0, i = 0, j = w) overwrites it
-            const unsigned accum = (k == 0 && i == 0 && j == w) ? 0u : 1u;
-            // A slice i serves the S - i products j = 0 .. S-1-i: it is read from shared memory once
-            // into the A collector buffer and reused by the following MMAs
-            const int uses = S - i;
-            if (uses == 1) umma_f16<0>(d_tmem, da, db, idesc, accum);
-            else if (j == 0) umma_f16<1>(d_tmem, da, db, idesc, accum);
-            else if (j < uses - 1) umma_f16<2>(d_tmem, da, db, idesc, accum);
-            else umma_f16<3>(d_tmem, da, db, idesc, accum);
-          }
-        }
+        const unsigned long long da = dA0 + (unsigned long long)((st * S * kTcA * 2) >> 4);
+        const unsigned long long db = dB0 + (unsigned long long)((st * S * kTcB * 2) >> 4);
+        // the first product of each accumulator in a tile (step 0, i = 0, j = w) overwrites it
+        if (k == 0) mma_kstep<S, true>(tmem, da, db, idesc);
+        else mma_kstep<S, false>(tmem, da, db, idesc);
         umma_commit(&empty[st]);
       }
       if (ok) umma_commit(&accbar);
@@ -715,49 +728,21 @@ __global__ void k_reduce_df(DFReduceArgs a) {
   }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// Tensor map over the slices [nmat][S][M][Kpad] seen as a 4-D tensor (8 elements, M rows, nmat S
-// slices, K/8 chunks) with strides (2 B, 2 Kpad B, 2 M Kpad B, 16 B): a box {8, 128, 1, 2} is one K
-// step of 16 for 128 rows of one slice (rows past M read as zeros), stored in shared memory as
-// [chunk][row][8 elements], i.e. 8-row x 16-byte core matrices, the next core matrix along K 2048
-// bytes further and the next 8-row group 128 bytes further.
-int encode_slice_map(SplitTable* t, int S) {
-  static EncodeTiledFn encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !fn) return VP_ERR_CUDA;
-    encode = reinterpret_cast<EncodeTiledFn>(fn);
-  }
-  const cuuint64_t row_bytes = (cuuint64_t)t->Kpad * sizeof(slice_t);
-  const cuuint64_t dims[4] = {8, (cuuint64_t)t->M, (cuuint64_t)t->nmat * S, (cuuint64_t)(t->Kpad / 8)};
-  const cuuint64_t strides[3] = {row_bytes, row_bytes * t->M, 16};
-  const cuuint32_t box[4] = {8, 128, 1, 2};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = encode(reinterpret_cast<CUtensorMap*>(t->tmap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, t->A, dims,
-                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? VP_OK : VP_ERR_CUDA;
-}
-
 constexpr int kKAlign = 32;  // padded K: a multiple of both engines' K steps
 int kpad(int K) { return (K + kKAlign - 1) / kKAlign * kKAlign; }
 
 int slice_table(const double* A, int nmat, int M, int K, int lda, long long mstride, int S, SplitTable* out,
                 cudaStream_t s) {
-  out->M = M; out->K = K; out->Kpad = kpad(K); out->nmat = nmat;
-  const size_t nh = (size_t)nmat * S * M * out->Kpad;
+  out->M = M; out->K = K; out->Kpad = kpad(K); out->nmat = nmat; out->nrt = (M + kSplitBM - 1) / kSplitBM;
+  const size_t nh = (size_t)nmat * out->nrt * kSplitBM * S * out->Kpad;
   TRY(cudaMalloc(&out->A, nh * sizeof(slice_t)));
+  TRY(cudaMemsetAsync(out->A, 0, nh * sizeof(slice_t), s));  // rows past M stay zero
   TRY(cudaMalloc(&out->ea, (size_t)nmat * M * sizeof(int)));
   const long long rows = (long long)nmat * M;
-  k_slice_rows<kSplitSlices><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(A, mstride, lda, M, K, out->Kpad,
-                                                                                 nmat, (slice_t*)out->A, out->ea);
+  k_slice_rows<kSplitSlices><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, s>>>(
+      A, mstride, lda, M, K, out->Kpad, nmat, out->nrt, (slice_t*)out->A, out->ea);
   TRY(cudaGetLastError());
-  return encode_slice_map(out, S);
+  return VP_OK;
 }
 
 }  // namespace
@@ -843,8 +828,7 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engin
   if (n_tiles <= 0) return VP_OK;
   if (engine == kEngineTcgen05) {
     const int grid = (short_ctas || n_tiles < g_num_sms) ? n_tiles : g_num_sms;
-    k_split_gemm_tc<kSplitSlices><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(
-        a, n_tiles, *static_cast<const CUtensorMap*>(a.tmap));
+    k_split_gemm_tc<kSplitSlices><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(a, n_tiles);
   }
   else
     k_split_gemm<kSplitSlices><<<n_tiles, 256, mma_smem_bytes(kSplitSlices), s>>>(a);

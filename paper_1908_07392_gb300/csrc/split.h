@@ -19,14 +19,16 @@ struct SplitTile {
   int group, m0, col0, ncol;
 };
 
-// One sliced operator family: slices [nmat][S][M][Kpad] (bf16) and row exponents [nmat][M].
+// One sliced operator family, stored tile by tile in the order the GEMM engines stage it: for matrix
+// mat, row tile rt (128 rows; rows past M are zero), K step ks (16) and slice s, one 4 KB block
+// [2 K chunks of 8][128 rows][8 elements] -- the canonical K-major core-matrix layout (8 rows x 16
+// bytes) of the tensor-core operand -- so the S slices of one K step of one row tile are 24 KB of
+// contiguous memory that one bulk copy moves. Layout [nmat][nrt][Kpad/16][S][2][128][8] (bf16) and
+// row exponents [nmat][M].
 struct SplitTable {
   void* A = nullptr;
   int* ea = nullptr;
-  int M = 0, K = 0, Kpad = 0, nmat = 0;
-  // TMA tensor map (CUtensorMap) over the slices, viewed as [K/8 chunks][rows][8 elements] so that a
-  // box lands in shared memory as 8-row x 16-byte core matrices (tcgen05 engine)
-  alignas(128) unsigned char tmap[128] = {};
+  int M = 0, K = 0, Kpad = 0, nmat = 0, nrt = 0;
 };
 
 // m2m_lo / m2m_hi: the multipole-to-multipole operator split by children (0-1 and 2-3) so that
@@ -37,7 +39,8 @@ struct SplitTables {
 
 struct SplitArgs {
   int M, Kpad, out_mode;        // out_mode 0: double-float slot (float2), 1: FP64 overwrite, 2: FP64 accumulate
-  const slice_t* A;
+  int nrt;                      // row tiles of 128 per operator matrix
+  const slice_t* A;             // tiled slices (SplitTable)
   const int* ea;
   const slice_t* B;             // sliced vectors [v][S][Kpad]
   const int* eb;
@@ -46,7 +49,6 @@ struct SplitArgs {
   const long long* a_mat;       // per group: matrix index
   const long long* src_vec;     // per column: vector index
   const long long* dst_off;     // per column: destination offset (elements of 8 bytes)
-  const void* tmap;             // host copy of the operator table's tensor map (tcgen05 engine)
 };
 
 struct DFReduceArgs {
