@@ -251,6 +251,62 @@ int vp_plan_pairs(int n_leaves, const int32_t* level, const int32_t* ix, const i
                   int32_t* tgt, int32_t* src, int32_t* mech);
 
 /*
+ * Layer potential at the nodes of a tree (Sec. 2.2, Eqs. uH_dbl, dbl_lyr_pot: the homogeneous part
+ * u^H = D[mu] of the velocity, as the boundary quadrature of Eq. dbl_lyr_quad; Sec. 3.2.1 for its
+ * fast evaluation): for a density mu given at boundary points y_j with unit normals n_j (pointing
+ * into the fluid domain, as for the boundary integral equation of bie.h) and quadrature weights w_j,
+ *
+ *     u_a(x) = sum_j D_ab(x, y_j) mu_b(y_j) w_j,   D_ab(x, y) = -T_bak(x - y) n_k(y),
+ *
+ * T the modified Stokes stresslet (App. B), at every node x of the tree (both velocity components).
+ * The far field goes through the tree's expansions: multipole coefficients of the sources of each
+ * leaf and local coefficients for the X lists come from sampling the kernel (split into its K0 and
+ * log r derived parts, the two channels of Eqs. mpole and loc) on a circle, and the tree's
+ * translation, multipole-to-local and target operators then apply as for the volume potential
+ * (split precision when the tables are VP_PREC_SPLIT); sources in leaves adjacent to a target leaf
+ * (and in the leaf itself) are summed directly in FP64 from matrices built at creation. Boxes
+ * without sources below them are left out of the upward pass. The values at nodes close to the
+ * boundary carry the error of the plain quadrature there, like the direct sum (Sec. 4 treats that).
+ *
+ * vp_layer_create -- bin the points into the tree's leaves and build the operators.
+ *  tree    a tree on VP_KERNEL_MBIHARMONIC tables (the two-channel bases; VP_ERR_ARG otherwise);
+ *          the layer uses the tree's tables (which must outlive it) but not its work buffers.
+ *  n_src   number of boundary points (>= 1).
+ *  src     HOST array [5][n_src]: x, y, n_x, n_y, w. Points must lie in the root box (VP_ERR_ARG).
+ *  stream  stream for the set-up; synchronised before returning.
+ * vp_layer_eval -- u (device [2][N]: u_x then u_y, node order as vp_eval) from mu (device
+ *  [n_src][2]: (mu_x, mu_y) per point, in the order given to vp_layer_create). Calls on one layer
+ *  must not overlap on the GPU; like vp_eval, the near part runs on `stream` while the far-field
+ *  chain runs on a side stream joined back before the output.
+ * vp_layer_steps -- vp_layer_eval with every launch timed in order, as vp_eval_steps.
+ * Errors: VP_ERR_ARG, VP_ERR_OOM, VP_ERR_CUDA.
+ */
+typedef struct vp_layer_s* vp_layer;
+int vp_layer_create(vp_tree tree, int n_src, const double* src, void* stream, vp_layer* out);
+int vp_layer_eval(vp_layer layer, const double* mu, double* u, void* stream);
+int vp_layer_steps(vp_layer layer, const double* mu, double* u, void* stream, int cap, int* n_steps, float* ms,
+                   int* info, double* flops, double* bytes);
+void vp_layer_free(vp_layer layer);
+
+/*
+ * Periodic particular solution by FFT (Sec. 2.1, Eqs. uhat, periodic_stokeslet, uP_Fourier,
+ * uP_Fourier_deriv; Sec. 3.1.2): for a force F sampled on the uniform n x n grid of a periodic box of
+ * side L (points x0 + i L/n, y0 + j L/n), the velocity of (alpha^2 - Laplacian) u + grad p = F,
+ * div u = 0 with Fourier multiplier S_hat(k) = (I - k k^T/|k|^2) / (alpha^2 + |k|^2) (S_hat(0) = I /
+ * alpha^2) and its gradient by Fourier differentiation (the Nyquist mode differentiates to zero).
+ * The paper feeds it the PUX extension of the force; here the caller supplies a periodic force.
+ * vp_periodic_create -- plan for alpha > 0, n a power of two in 32..4096, side L > 0 (work arrays of
+ *  4 n^2 complex doubles on the device; synchronises `stream`).
+ * vp_periodic_eval -- F device [2][n][n] (component, row j, column i), u device [2][n][n], gradu
+ *  device [2][2][n][n] with gradu[a][m] = d u_a / d x_m. Calls on one plan must not overlap.
+ * Errors: VP_ERR_ARG, VP_ERR_OOM, VP_ERR_CUDA.
+ */
+typedef struct vp_periodic_s* vp_periodic;
+int vp_periodic_create(double alpha, int n, double side, void* stream, vp_periodic* out);
+int vp_periodic_eval(vp_periodic plan, const double* F, double* u, double* gradu, void* stream);
+void vp_periodic_free(vp_periodic plan);
+
+/*
  * vp_eval_static -- vp_eval that allocates nothing.
  *
  * For callers that cannot call cudaMalloc (or any allocating routine) at the

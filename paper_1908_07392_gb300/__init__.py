@@ -95,6 +95,17 @@ def load_library():
     lib.vp_eval_timed.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, ctypes.POINTER(ctypes.c_float)]
     lib.vp_tree_stats.argtypes = [c_void_p, i64p, ctypes.POINTER(c_double)]
     lib.vp_tree_bytes.argtypes = [c_void_p, ctypes.POINTER(c_double)]
+    lib.vp_layer_create.argtypes = [c_void_p, c_int, c_void_p, c_void_p, ctypes.POINTER(c_void_p)]
+    lib.vp_layer_eval.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.vp_layer_steps.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.POINTER(c_int),
+                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int), ctypes.POINTER(c_double),
+                                   ctypes.POINTER(c_double)]
+    lib.vp_layer_free.argtypes = [c_void_p]
+    lib.vp_layer_free.restype = None
+    lib.vp_periodic_create.argtypes = [c_double, c_int, c_double, c_void_p, ctypes.POINTER(c_void_p)]
+    lib.vp_periodic_eval.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.vp_periodic_free.argtypes = [c_void_p]
+    lib.vp_periodic_free.restype = None
     lib.vp_eval_steps.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.POINTER(c_int),
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int), ctypes.POINTER(c_double),
                                   ctypes.POINTER(c_double)]
@@ -112,7 +123,8 @@ def load_library():
 def exported_symbols():
     """Names declared in include/vp.h (the ABI surface)."""
     return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_tree_interp", "vp_special", "vp_eval", "vp_eval_host",
-            "vp_eval_timed", "vp_tree_stats", "vp_tree_bytes", "vp_eval_steps", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
+            "vp_eval_timed", "vp_tree_stats", "vp_tree_bytes", "vp_eval_steps", "vp_layer_create", "vp_layer_eval",
+            "vp_layer_steps", "vp_layer_free", "vp_periodic_create", "vp_periodic_eval", "vp_periodic_free", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
             "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status", "vp_selftest_timeout",
             "bie_create", "bie_free", "bie_size", "bie_nodes", "bie_apply", "bie_solve", "bie_solve_aug", "bie_eval",
@@ -268,6 +280,69 @@ def vp_eval_steps(tree: int, f, u, gradu, stream=None):
                              fl, by), "vp_eval_steps")
     return [{"ms": ms[i], "kind": info[4 * i], "stage": info[4 * i + 1], "table": info[4 * i + 2],
              "engine": info[4 * i + 3], "flops": fl[i], "bytes": by[i]} for i in range(k)]
+
+
+def vp_layer_create(tree: int, src, stream=None) -> int:
+    """Layer potential operators of boundary points on a tree. src: host array [5][n] (x, y, n_x, n_y, w)."""
+    a = np.ascontiguousarray(src, dtype=np.float64)
+    if a.ndim != 2 or a.shape[0] != 5:
+        raise ValueError("src must be [5][n]: x, y, n_x, n_y, w")
+    out = ctypes.c_void_p()
+    _check(load_library().vp_layer_create(ctypes.c_void_p(tree), int(a.shape[1]), a.ctypes.data_as(ctypes.c_void_p),
+                                          _stream_ptr(stream), ctypes.byref(out)), "vp_layer_create")
+    return out.value
+
+
+def vp_layer_eval(layer: int, mu, u, stream=None):
+    """mu: device float64 [n][2] (or [2n], (mu_x, mu_y) per point); u: device float64 [2, N]."""
+    _check(load_library().vp_layer_eval(ctypes.c_void_p(layer), ctypes.c_void_p(mu.data_ptr()),
+                                        ctypes.c_void_p(u.data_ptr()), _stream_ptr(stream)), "vp_layer_eval")
+
+
+def vp_layer_steps(layer: int, mu, u, stream=None):
+    """Every launch of one layer evaluation timed in order (as vp_eval_steps)."""
+    lib = load_library()
+    n = ctypes.c_int()
+    _check(lib.vp_layer_steps(ctypes.c_void_p(layer), None, None, _stream_ptr(stream), 0, ctypes.byref(n),
+                              None, None, None, None), "vp_layer_steps")
+    k = n.value
+    ms = (ctypes.c_float * k)(); info = (ctypes.c_int * (4 * k))()
+    fl = (ctypes.c_double * k)(); by = (ctypes.c_double * k)()
+    _check(lib.vp_layer_steps(ctypes.c_void_p(layer), ctypes.c_void_p(mu.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                              _stream_ptr(stream), k, ctypes.byref(n), ms, info, fl, by), "vp_layer_steps")
+    return [{"ms": ms[i], "kind": info[4 * i], "stage": info[4 * i + 1], "table": info[4 * i + 2],
+             "engine": info[4 * i + 3], "flops": fl[i], "bytes": by[i]} for i in range(k)]
+
+
+class PeriodicStokes:
+    """Periodic particular solution by FFT on an n x n grid of a box of side L (include/vp.h)."""
+
+    def __init__(self, alpha, n, side, stream=None):
+        out = ctypes.c_void_p()
+        _check(load_library().vp_periodic_create(float(alpha), int(n), float(side), _stream_ptr(stream),
+                                                 ctypes.byref(out)), "vp_periodic_create")
+        self.handle, self.n, self.alpha, self.side = out.value, n, alpha, side
+
+    def __call__(self, F, u=None, gradu=None, stream=None):
+        """F device float64 [2, n, n] -> u [2, n, n], gradu [2, 2, n, n]."""
+        import torch
+        n = self.n
+        u = torch.empty(2, n, n, dtype=torch.float64, device=F.device) if u is None else u
+        gradu = torch.empty(2, 2, n, n, dtype=torch.float64, device=F.device) if gradu is None else gradu
+        _check(load_library().vp_periodic_eval(ctypes.c_void_p(self.handle), ctypes.c_void_p(F.data_ptr()),
+                                               ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(gradu.data_ptr()),
+                                               _stream_ptr(stream)), "vp_periodic_eval")
+        return u, gradu
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().vp_periodic_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+def vp_layer_free(layer: int):
+    if layer:
+        load_library().vp_layer_free(ctypes.c_void_p(layer))
 
 
 def vp_eval_host(tree: int, f, u, gradu, stream=None):

@@ -25,6 +25,7 @@
 #include <new>
 #include <vector>
 
+#include "layer.h"
 #include "plan.h"
 #include "split.h"
 #include "vp_internal.h"
@@ -254,6 +255,7 @@ struct HostGemm {
   // split precision: source vector family (-1: always FP64; 0: leaf values, 1: (box, channel)
   // multipoles, 2: box locals) and output (0: double-float slot, 1: FP64 overwrite, 2: FP64 accumulate)
   int split_vec = -1, out_mode = 0;
+  long long mat_elems = 0;  // elements of one operator matrix (0: M * lda; set when M is a leading part)
   struct Entry { long long a, s, d, v = -1; };  // v: sliced-vector id (split), -1 = derived from s
   std::vector<Entry> entries;
 };
@@ -295,8 +297,18 @@ struct DevSlice {
 
 enum Table { T_NEAR, T_S2M, T_L2T, T_M2M, T_L2L, T_M2L, T_M2T, T_S2L, T_M2M_LO, T_M2M_HI };
 
+// A point-source operator launch (layer potential): instances of small dense matrices applied to the
+// boundary density (layer.h), written into buffer `dst`.
+struct DevPt {
+  PtInst* inst = nullptr;
+  int n_inst = 0, rows = 0, rb = 0, dst = 0;
+  long long bs = 0;
+  double* A = nullptr;
+};
+
 struct Step {
-  int kind;   // 0 gemm, 1 reduce, 2 memset mp, 3 slice vectors, 4 split gemm, 5 double-float reduce
+  int kind;   // 0 gemm, 1 reduce, 2 memset mp, 3 slice vectors, 4 split gemm, 5 double-float reduce,
+              // 6 point-source operator
   int index;
   int stage;  // VP_STAGE_* for timing
   double flops = 0.0;  // algorithmic floating-point operations of the step
@@ -315,6 +327,7 @@ struct vp_tree_s {
   double* d_xi = nullptr;
   double *mp = nullptr, *loc = nullptr, *lslot = nullptr, *uslot = nullptr;
   long long n_lslot = 0, n_uslot = 0;
+  int lslot_stride = 0, uslot_stride = 0;  // slot strides of a layer program (even: 16-byte aligned slots)
   std::vector<void*> allocs;  // every device allocation owned by the tree
   std::vector<vp::DevGemm> gemms;
   std::vector<vp::DevReduce> reduces;
@@ -332,6 +345,13 @@ struct vp_tree_s {
   double *d_f = nullptr, *d_u = nullptr, *d_g = nullptr;
   // point location for vp_tree_interp: finest-level cell -> leaf, built on first use
   int* d_cell = nullptr;
+  // host copy of the leaf list (level, ix, iy), kept for programs built later on the same tree
+  std::vector<int> h_lv, h_ix, h_iy;
+  // layer-potential program: multipole buffer size (0: n_boxes * E), point-source operators and
+  // the source permutation they read the density through
+  long long mp_elems = 0;
+  std::vector<vp::DevPt> pts;
+  int* d_perm = nullptr;
   // overlap of the near field with the far-field chain (vp_eval): the chain runs on `side`, a
   // high-priority stream, the near field on the caller's stream; events fork and join them
   cudaStream_t side = nullptr;
@@ -412,7 +432,7 @@ int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
   const vp_tables_s* T = tr->T;
   std::stable_sort(g.entries.begin(), g.entries.end(),
                    [](const HostGemm::Entry& x, const HostGemm::Entry& y) { return x.a < y.a; });
-  const long long mat_elems = (long long)g.M * g.lda;
+  const long long mat_elems = g.mat_elems ? g.mat_elems : (long long)g.M * g.lda;
   const long long vec_len = g.split_vec == 0 ? T->n : (g.split_vec == 1 ? T->C : T->E);  // families 0-2
   std::vector<long long> a_mat, src_vec, dst_off;
   std::vector<SplitTile> tiles[2];
@@ -720,6 +740,286 @@ int build_tree(vp_tree_s* tr, const TreePlan& P, cudaStream_t s) {
   return VP_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Layer-potential program (vp_layer_*): the double-layer velocity of boundary point sources at every
+// node of the tree, both components, through the same grouped contractions as the volume
+// potential. Boxes whose subtree holds no source carry no multipole and are left out of the
+// upward pass and of the source side of the V and W lists; every box still receives locals and
+// every leaf its values. Point-source operators (layer.cu) replace the leaf sources: multipoles
+// of source leaves, locals of X-list targets, and direct values for adjacent (U-list) leaves.
+
+// Sources binned by leaf box: sources perm[first[b] .. first[b] + count[b]) lie in box b.
+struct LayerBins {
+  std::vector<int> first, count;
+  int max_ns = 0;
+};
+
+int upload_pt(vp_tree_s* tr, std::vector<PtInst>& inst, int rows, int rb, long long bs, int dst_buf, int kind,
+              const PtSources& S, cudaStream_t s) {
+  if (inst.empty()) return VP_OK;
+  const vp_tables_s* T = tr->T;
+  long long total = 0;
+  int max_ns = 0;
+  double fl = 0.0;
+  for (PtInst& I : inst) {
+    I.aoff = total;
+    total += (long long)rows * 2 * I.ns;
+    max_ns = std::max(max_ns, I.ns);
+    fl += 2.0 * rows * 2.0 * I.ns;
+  }
+  DevPt d;
+  d.n_inst = (int)inst.size(); d.rows = rows; d.rb = rb; d.bs = bs; d.dst = dst_buf;
+  int rc;
+  if ((rc = dev_upload(tr, inst, &d.inst, s))) return rc;
+  void* A = nullptr;
+  TRY(cudaMalloc(&A, (size_t)total * sizeof(double)));
+  tr->allocs.push_back(A);
+  d.A = static_cast<double*>(A);
+  if (kind == 2) rc = launch_pt_near(T->alpha, T->p, tr->d_xi, d.inst, d.n_inst, max_ns, S, d.A, s);
+  else rc = launch_pt_coeffs(kind, T->alpha, T->P, d.inst, d.n_inst, max_ns, S, d.A, s);
+  if (rc) return rc;
+  const double by = 8.0 * (double)total + 8.0 * (double)rows * (double)inst.size();
+  tr->steps.push_back({6, (int)tr->pts.size(), tr->cur_stage, fl, by});
+  tr->flops[tr->cur_stage] += fl;
+  tr->bytes[tr->cur_stage] += by;
+  tr->pts.push_back(d);
+  return VP_OK;
+}
+
+int build_layer(vp_tree_s* tr, const TreePlan& P, const LayerBins& bins, const PtSources& S, cudaStream_t s) {
+  const vp_tables_s* T = tr->T;
+  const int n = T->n, C = T->C, E = T->E, nch = T->nch;
+  constexpr int NC = 2;                  // velocity components
+  const int Cs = (C + 1) & ~1, Us = (n + 1) & ~1;
+  tr->lslot_stride = Cs;
+  tr->uslot_stride = Us;
+  const auto& B = P.boxes;
+  const long long NB = (long long)B.size();
+  auto kact = [&](int l) { return l >= 0 && l <= T->levels && T->kactive[l]; };
+  auto off = [&](int a, long long b) { return (a * NB + b) * E; };  // coefficients of (component, box)
+  const double x0 = tr->cx - 0.5 * T->side, y0 = tr->cy - 0.5 * T->side;
+  // boxes whose subtree holds sources (children are numbered after their parent)
+  std::vector<char> has(NB, 0);
+  for (long long i = NB - 1; i >= 0; --i) {
+    if (B[i].leaf >= 0) has[i] = bins.count[i] > 0;
+    else
+      for (int q = 0; q < 4; ++q) has[i] |= has[B[i].child0 + q];
+  }
+  std::vector<std::vector<long long>> lsl((size_t)NC * NB * nch), usl((size_t)NC * NB);
+  long long nls = 0, nus = 0;
+
+  std::vector<PtInst> ps2m, ps2l, pnear;
+  for (long long i = 0; i < NB; ++i) {
+    const Box& b = B[i];
+    if (b.leaf < 0 || b.level < 2 || bins.count[i] == 0) continue;
+    const double h = T->h(b.level), r = h / std::sqrt(2.0);
+    PtInst I{};
+    I.cx = x0 + (b.ix + 0.5) * h; I.cy = y0 + (b.iy + 0.5) * h; I.R = 1.25 * r; I.r = r;
+    I.j0 = bins.first[i]; I.ns = bins.count[i]; I.kact = kact(b.level); I.dst = off(0, i);
+    ps2m.push_back(I);
+  }
+  HostGemm m2l, l2t, m2t;
+  m2l.M = C; m2l.K = C; m2l.lda = C; m2l.table = T_M2L; m2l.src = BUF_MP; m2l.dst = BUF_LSLOT; m2l.split_vec = 1;
+  for (const Pair& v : P.V) {
+    if (!has[v.src]) continue;
+    const int l = B[v.tgt].level;
+    for (int a = 0; a < NC; ++a)
+      for (int ch = 0; ch < nch; ++ch) {
+        if (ch == 0 && !kact(l)) continue;
+        const long long slot = nls++;
+        lsl[(size_t)(a * NB + v.tgt) * nch + ch].push_back(slot * Cs);
+        m2l.entries.push_back({(long long)(l * T->m2l_stride_lvl() + v.pos * T->m2l_stride_off() + ch * T->m2l_stride_ch()),
+                               off(a, v.src) + ch * C, slot * Cs});
+      }
+  }
+  for (const Pair& x : P.X) {
+    if (bins.count[x.src] == 0) continue;
+    const Box& b = B[x.tgt];
+    const double h = T->h(b.level), r = h / std::sqrt(2.0);
+    const long long base = nls;
+    nls += NC * nch;
+    for (int a = 0; a < NC; ++a)
+      for (int ch = 0; ch < nch; ++ch) lsl[(size_t)(a * NB + x.tgt) * nch + ch].push_back((base + a * nch + ch) * Cs);
+    PtInst I{};
+    I.cx = x0 + (b.ix + 0.5) * h; I.cy = y0 + (b.iy + 0.5) * h; I.R = r; I.r = r;
+    I.j0 = bins.first[x.src]; I.ns = bins.count[x.src]; I.kact = kact(b.level); I.dst = base * Cs;
+    ps2l.push_back(I);
+  }
+  l2t.M = n; l2t.K = E; l2t.lda = E; l2t.table = T_L2T; l2t.src = BUF_LOC; l2t.dst = BUF_USLOT; l2t.split_vec = 2;
+  l2t.mat_elems = (long long)3 * n * E;  // values only: the leading n rows of the [3n x E] operator
+  for (long long i = 0; i < NB; ++i) {
+    const Box& b = B[i];
+    if (b.leaf < 0 || b.level < 2) continue;
+    for (int a = 0; a < NC; ++a) {
+      const long long slot = nus++;
+      usl[a * NB + i].push_back(slot * Us);
+      l2t.entries.push_back({(long long)(b.level * T->l2t_stride_lvl()), off(a, i), slot * Us});
+    }
+  }
+  m2t.M = n; m2t.K = C; m2t.lda = C; m2t.table = T_M2T; m2t.src = BUF_MP; m2t.dst = BUF_USLOT; m2t.split_vec = 1;
+  m2t.mat_elems = (long long)3 * n * C;
+  for (const Pair& w : P.W) {
+    if (!has[w.src]) continue;
+    const int l = B[w.tgt].level;
+    for (int a = 0; a < NC; ++a)
+      for (int ch = 0; ch < nch; ++ch) {
+        if (ch == 0 && !kact(l + 1)) continue;
+        const long long slot = nus++;
+        usl[a * NB + w.tgt].push_back(slot * Us);
+        m2t.entries.push_back({(long long)(l * T->m2t_stride_lvl() + w.pos * T->m2t_stride_pos() + ch * T->m2t_stride_ch()),
+                               off(a, w.src) + ch * C, slot * Us});
+      }
+  }
+  for (const Pair& u : P.U) {
+    if (bins.count[u.src] == 0) continue;
+    const Box& b = B[u.tgt];
+    const double h = T->h(b.level);
+    const long long base = nus;
+    nus += NC;
+    for (int a = 0; a < NC; ++a) usl[a * NB + u.tgt].push_back((base + a) * Us);
+    PtInst I{};
+    I.cx = x0 + b.ix * h; I.cy = y0 + b.iy * h; I.R = h; I.r = h;
+    I.j0 = bins.first[u.src]; I.ns = bins.count[u.src]; I.kact = 1; I.dst = base * Us;
+    pnear.push_back(I);
+  }
+  tr->n_lslot = nls;
+  tr->n_uslot = nus;
+
+  // ---- device buffers
+  tr->mp_elems = NC * NB * E;
+  TRY(cudaMalloc(&tr->mp, std::max<long long>(1, NC * NB * E) * sizeof(double)));
+  tr->allocs.push_back(tr->mp);
+  TRY(cudaMalloc(&tr->loc, std::max<long long>(1, NC * NB * E) * sizeof(double)));
+  tr->allocs.push_back(tr->loc);
+  TRY(cudaMalloc(&tr->lslot, std::max<long long>(1, nls * Cs) * sizeof(double)));
+  tr->allocs.push_back(tr->lslot);
+  TRY(cudaMalloc(&tr->uslot, std::max<long long>(1, nus * Us) * sizeof(double)));
+  tr->allocs.push_back(tr->uslot);
+  const bool split = T->precision == VP_PREC_SPLIT;
+  if (split) {
+    const long long nv[kVecFamilies] = {1, NC * NB * nch, NC * NB, NC * NB * nch, NC * NB * nch, NC * NB * nch};
+    const int kk[kVecFamilies] = {n, C, E, 2 * C, C, 2 * C};
+    for (int v = 0; v < kVecFamilies; ++v) {
+      TRY(cudaMalloc(&tr->sv[v], std::max<long long>(1, nv[v] * kSplitSlices * split_kpad(kk[v])) * 2));
+      tr->allocs.push_back(tr->sv[v]);
+      TRY(cudaMalloc(&tr->se[v], std::max<long long>(1, nv[v]) * sizeof(int)));
+      tr->allocs.push_back(tr->se[v]);
+    }
+  }
+
+  int rc;
+  tr->cur_stage = VP_STAGE_UPWARD;
+  tr->steps.push_back({2, 0, tr->cur_stage, 0.0, 8.0 * (double)(NC * NB * E)});
+  tr->bytes[tr->cur_stage] += 8.0 * (double)(NC * NB * E);
+  if ((rc = upload_pt(tr, ps2m, 2 * E, E, NB * E, BUF_MP, 0, S, s))) return rc;
+  for (int l = P.max_level - 1; l >= 2; --l) {
+    if (!split) {
+      HostGemm m2m;
+      m2m.M = C; m2m.K = 4 * C; m2m.kseg = C; m2m.seg_stride = E; m2m.lda = 4 * C; m2m.table = T_M2M;
+      m2m.src = BUF_MP; m2m.dst = BUF_MP;
+      for (long long i = 0; i < NB; ++i) {
+        if (B[i].level != l || B[i].leaf >= 0 || !has[i]) continue;
+        for (int a = 0; a < NC; ++a)
+          for (int ch = 0; ch < nch; ++ch) {
+            if (ch == 0 && !kact(l)) continue;
+            m2m.entries.push_back({(long long)(l * T->m2m_stride_lvl() + ch * T->m2m_stride_ch()),
+                                   off(a, B[i].child0) + ch * C, off(a, i) + ch * C});
+          }
+      }
+      if ((rc = upload_gemm(tr, m2m, s))) return rc;
+      continue;
+    }
+    for (int half = 0; half < 2; ++half) {
+      HostGemm m2m;
+      m2m.M = C; m2m.K = 2 * C; m2m.kseg = C; m2m.seg_stride = E; m2m.lda = 4 * C;
+      m2m.table = half ? T_M2M_HI : T_M2M_LO;
+      m2m.src = BUF_MP; m2m.dst = BUF_MP; m2m.split_vec = half ? 5 : 3; m2m.out_mode = half ? 2 : 1;
+      std::vector<long long> sbase, svid;
+      for (long long i = 0; i < NB; ++i) {
+        if (B[i].level != l || B[i].leaf >= 0 || !has[i]) continue;
+        for (int a = 0; a < NC; ++a)
+          for (int ch = 0; ch < nch; ++ch) {
+            if (ch == 0 && !kact(l)) continue;
+            const long long src = off(a, B[i].child0 + 2 * half) + ch * C;
+            const long long vid = (a * NB + i) * nch + ch;
+            m2m.entries.push_back({(long long)(l * T->m2m_stride_lvl() + ch * T->m2m_stride_ch()), src,
+                                   off(a, i) + ch * C, vid});
+            sbase.push_back(src);
+            svid.push_back(vid);
+          }
+      }
+      if ((rc = add_slice(tr, half ? 5 : 3, BUF_MP, 2 * C, C, E, 0, (long long)svid.size(), &sbase, &svid, s)))
+        return rc;
+      if ((rc = upload_gemm(tr, m2m, s))) return rc;
+    }
+  }
+  tr->cur_stage = VP_STAGE_M2L;
+  if (split && (rc = add_slice(tr, 1, BUF_MP, C, C, 0, C, NC * NB * nch, nullptr, nullptr, s))) return rc;
+  if ((rc = upload_gemm(tr, m2l, s))) return rc;
+  if ((rc = upload_pt(tr, ps2l, 2 * E, C, Cs, BUF_LSLOT, 1, S, s))) return rc;
+  tr->cur_stage = VP_STAGE_DOWNWARD;
+  {
+    HostReduce r;
+    r.M = C; r.dst = BUF_LOC; r.src = BUF_LSLOT;
+    r.ptr.push_back(0);
+    for (int a = 0; a < NC; ++a)
+      for (long long i = 0; i < NB; ++i) {
+        if (B[i].level < 2) continue;
+        for (int ch = 0; ch < nch; ++ch) {
+          r.dst_off.push_back(off(a, i) + ch * C);
+          for (long long o : lsl[(size_t)(a * NB + i) * nch + ch]) r.slot.push_back(o);
+          r.ptr.push_back((long long)r.slot.size());
+        }
+      }
+    if ((rc = upload_reduce(tr, r, s))) return rc;
+  }
+  for (int l = 3; l <= P.max_level; ++l) {
+    HostGemm l2l;
+    l2l.M = C; l2l.K = C; l2l.lda = C; l2l.accumulate = 1; l2l.table = T_L2L; l2l.src = BUF_LOC; l2l.dst = BUF_LOC;
+    l2l.split_vec = 4; l2l.out_mode = 2;
+    std::vector<long long> sbase, svid;
+    for (long long i = 0; i < NB; ++i) {
+      if (B[i].level != l) continue;
+      const int par = B[i].parent;
+      const int q = (int)(i - B[par].child0);
+      for (int a = 0; a < NC; ++a)
+        for (int ch = 0; ch < nch; ++ch) {
+          if (ch == 0 && !kact(l - 1)) continue;
+          const long long vid = (a * NB + par) * nch + ch;
+          l2l.entries.push_back({(long long)((l - 1) * T->l2l_stride_lvl() + q * T->l2l_stride_q() + ch * T->l2l_stride_ch()),
+                                 off(a, par) + ch * C, off(a, i) + ch * C, vid});
+          if (q == 0) {
+            sbase.push_back(off(a, par) + ch * C);
+            svid.push_back(vid);
+          }
+        }
+    }
+    if (split && (rc = add_slice(tr, 4, BUF_LOC, C, C, 0, 0, (long long)svid.size(), &sbase, &svid, s))) return rc;
+    if ((rc = upload_gemm(tr, l2l, s))) return rc;
+  }
+  tr->cur_stage = VP_STAGE_TARGETS;
+  if (split && (rc = add_slice(tr, 2, BUF_LOC, E, E, 0, E, NC * NB, nullptr, nullptr, s))) return rc;
+  if ((rc = upload_gemm(tr, l2t, s))) return rc;
+  if ((rc = upload_gemm(tr, m2t, s))) return rc;
+  tr->cur_stage = VP_STAGE_NEAR;
+  if ((rc = upload_pt(tr, pnear, 2 * n, n, Us, BUF_USLOT, 2, S, s))) return rc;
+  tr->cur_stage = VP_STAGE_OUTPUT;
+  {
+    HostReduce r;
+    r.M = n; r.final_out = 1; r.src = BUF_USLOT;
+    r.ptr.push_back(0);
+    for (int a = 0; a < NC; ++a)
+      for (int k = 0; k < tr->n_leaves; ++k) {
+        const int bi = P.leaf_box[k];
+        r.dst_off.push_back(a * tr->N + (long long)k * n);
+        for (long long o : usl[a * NB + bi]) r.slot.push_back(o);
+        r.ptr.push_back((long long)r.slot.size());
+      }
+    if ((rc = upload_reduce(tr, r, s))) return rc;
+  }
+  return VP_OK;
+}
+
 // Kernel arguments of one split-precision launch with the engine set in d.
 SplitArgs split_args(const vp_tree_s* tr, const DevSplit& d, double* const* bufs) {
   const SplitTables* stt = static_cast<const SplitTables*>(tr->T->near_split);
@@ -731,6 +1031,7 @@ SplitArgs split_args(const vp_tree_s* tr, const DevSplit& d, double* const* bufs
   a.A = static_cast<const slice_t*>(tb->A);
   a.ea = tb->ea;
   a.nrt = tb->nrt;
+  a.ea_ld = tb->M;
   a.B = static_cast<const slice_t*>(tr->sv[d.vec]);
   a.eb = tr->se[d.vec];
   a.Y = bufs[d.dst];
@@ -776,7 +1077,8 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
     }
     const cudaStream_t s = (!overlap || near_step || st.stage == VP_STAGE_OUTPUT) ? s0 : tr->side;
     if (st.kind == 2) {
-      TRY(cudaMemsetAsync(tr->mp, 0, (size_t)tr->n_boxes * T->E * sizeof(double), s));
+      const long long elems = tr->mp_elems ? tr->mp_elems : (long long)tr->n_boxes * T->E;
+      TRY(cudaMemsetAsync(tr->mp, 0, (size_t)elems * sizeof(double), s));
     } else if (st.kind == 0) {
       const DevGemm& d = tr->gemms[st.index];
       GemmArgs a = d.args;
@@ -795,6 +1097,11 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
       if (a.M > 4 * threads) return VP_ERR_ARG;  // at most 4 rows per thread (3 p^2 <= 768)
       k_reduce<<<d.n_dst, threads, 0, s>>>(a);
       TRY(cudaGetLastError());
+    } else if (st.kind == 6) {
+      const DevPt& d = tr->pts[st.index];
+      const int rc = launch_pt_apply(d.rows, d.rb, d.bs, d.inst, d.n_inst, tr->d_perm, bufs_c[BUF_F], d.A,
+                                     bufs[d.dst], s);
+      if (rc) return rc;
     } else if (st.kind == 3) {
       const DevSlice& d = tr->slice_ops[st.index];
       const int rc = launch_slice_list(bufs_c[d.buf], d.base, d.vid, d.n, d.K, d.kseg, d.seg_stride, d.cstride,
@@ -855,6 +1162,7 @@ extern "C" int vp_tree_upload(vp_tables tables, double cx, double cy, int n_leav
   auto fail = [&](int code) { vp_tree_free(tr.release()); return code; };
   {
     std::vector<int> lv(level, level + n_leaves), xx(ix, ix + n_leaves), yy(iy, iy + n_leaves);
+    tr->h_lv = lv; tr->h_ix = xx; tr->h_iy = yy;
     if ((rc = dev_upload(tr.get(), lv, &tr->d_lv, s))) return fail(rc);
     if ((rc = dev_upload(tr.get(), xx, &tr->d_ix, s))) return fail(rc);
     if ((rc = dev_upload(tr.get(), yy, &tr->d_iy, s))) return fail(rc);
@@ -1339,6 +1647,112 @@ extern "C" int vp_eval_batched(int n_trees, const vp_tree* trees, const double* 
     if (rc) return rc;
   }
   return VP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Layer potential at the nodes of a tree (vp_layer_*).
+struct vp_layer_s {
+  vp_tree_s* prog = nullptr;  // the step program over the tree's boxes (owns its buffers)
+  int n_src = 0;
+};
+
+extern "C" int vp_layer_create(vp_tree tree, int n_src, const double* src, void* stream, vp_layer* out) {
+  if (!out) return VP_ERR_ARG;
+  *out = nullptr;
+  if (!tree || n_src < 1 || !src) return VP_ERR_ARG;
+  vp_tables_s* T = tree->T;
+  if (T->nch != 2) return VP_ERR_ARG;  // the double layer needs the two-channel (modified-biharmonic) bases
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  TreePlan P;
+  int rc = build_plan(tree->n_leaves, tree->h_lv.data(), tree->h_ix.data(), tree->h_iy.data(), T->levels, P);
+  if (rc != VP_OK) return rc;
+  const auto& B = P.boxes;
+  const long long NB = (long long)B.size();
+  // bin the sources by leaf box (descending from the root; a point on a box edge goes to the child
+  // above / to the right)
+  const double x0 = tree->cx - 0.5 * T->side, y0 = tree->cy - 0.5 * T->side;
+  std::vector<int> box_of(n_src);
+  for (int j = 0; j < n_src; ++j) {
+    const double x = src[j], y = src[n_src + j];
+    if (!std::isfinite(x) || !std::isfinite(y) || x < x0 || y < y0 || x > x0 + T->side || y > y0 + T->side)
+      return VP_ERR_ARG;
+    const double w = src[4 * (size_t)n_src + j];
+    if (!std::isfinite(w) || !std::isfinite(src[2 * (size_t)n_src + j]) || !std::isfinite(src[3 * (size_t)n_src + j]))
+      return VP_ERR_ARG;
+    int b = 0;
+    while (B[b].leaf < 0) {
+      const double h = T->h(B[b].level);
+      const double cx = x0 + (B[b].ix + 0.5) * h, cy = y0 + (B[b].iy + 0.5) * h;
+      b = B[b].child0 + (x >= cx ? 1 : 0) + (y >= cy ? 2 : 0);
+    }
+    box_of[j] = b;
+  }
+  LayerBins bins;
+  bins.first.assign(NB, 0);
+  bins.count.assign(NB, 0);
+  for (int j = 0; j < n_src; ++j) ++bins.count[box_of[j]];
+  {
+    int acc = 0;
+    for (long long b = 0; b < NB; ++b) { bins.first[b] = acc; acc += bins.count[b]; bins.max_ns = std::max(bins.max_ns, bins.count[b]); }
+  }
+  std::vector<int> perm(n_src), fill(bins.first);
+  for (int j = 0; j < n_src; ++j) perm[fill[box_of[j]]++] = j;
+
+  std::unique_ptr<vp_tree_s> pr(new (std::nothrow) vp_tree_s());
+  if (!pr) return VP_ERR_OOM;
+  pr->T = T;
+  pr->n_leaves = tree->n_leaves;
+  pr->n_boxes = (int)NB;
+  pr->max_level = P.max_level;
+  pr->N = tree->N;
+  pr->cx = tree->cx; pr->cy = tree->cy;
+  auto fail = [&](int code) { vp_tree_free(pr.release()); return code; };
+  {
+    std::vector<double> xi(T->p), w(T->p);
+    gauss_legendre_host(T->p, xi.data(), w.data());
+    if ((rc = dev_upload(pr.get(), xi, &pr->d_xi, s))) return fail(rc);
+  }
+  std::vector<double> sv(src, src + 5 * (size_t)n_src);
+  double* d_src = nullptr;
+  if ((rc = dev_upload(pr.get(), sv, &d_src, s))) return fail(rc);
+  if ((rc = dev_upload(pr.get(), perm, &pr->d_perm, s))) return fail(rc);
+  PtSources S{d_src, d_src + n_src, d_src + 2 * (size_t)n_src, d_src + 3 * (size_t)n_src, d_src + 4 * (size_t)n_src,
+              pr->d_perm};
+  if ((rc = build_layer(pr.get(), P, bins, S, s))) return fail(rc);
+  {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&pr->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pr->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pr->ev_src, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pr->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return fail(VP_ERR_CUDA);
+  }
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { set_last_cuda(e); return fail(VP_ERR_CUDA); }
+  std::unique_ptr<vp_layer_s> L(new (std::nothrow) vp_layer_s());
+  if (!L) return fail(VP_ERR_OOM);
+  L->prog = pr.release();
+  L->n_src = n_src;
+  *out = L.release();
+  return VP_OK;
+}
+
+extern "C" int vp_layer_eval(vp_layer layer, const double* mu, double* u, void* stream) {
+  if (!layer || !mu || !u) return VP_ERR_ARG;
+  return run_steps(layer->prog, mu, u, u, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int vp_layer_steps(vp_layer layer, const double* mu, double* u, void* stream, int cap, int* n_steps,
+                              float* ms, int* info, double* flops, double* bytes) {
+  if (!layer) return VP_ERR_ARG;
+  return vp_eval_steps(layer->prog, mu, u, u, stream, cap, n_steps, ms, info, flops, bytes);
+}
+
+extern "C" void vp_layer_free(vp_layer layer) {
+  if (!layer) return;
+  vp_tree_free(layer->prog);
+  delete layer;
 }
 
 // ---------------------------------------------------------------------------

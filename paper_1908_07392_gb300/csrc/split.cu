@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
   const long long mat = a.a_mat[tile.group];
   // this tile's rows in the tiled operator layout: [K step][slice][chunk][128 rows][8]
   const slice_t* Ag = a.A + (mat * a.nrt + (tile.m0 >> 7)) * (long long)(a.Kpad / 16) * S * 2048;
-  const int* ea = a.ea + mat * a.M;
+  const int* ea = a.ea + mat * a.ea_ld;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp & 3, wn = warp >> 2;  // 4 warps along M (32 rows), 2 along N (32 columns)
   const int gid = lane >> 2, tig = lane & 3;
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       const int row = tile.m0 + q * 32 + lane;
       const bool row_ok = row < a.M;
-      const int era = row_ok ? a.ea[a.a_mat[tile.group] * a.M + row] : 0;
+      const int era = row_ok ? a.ea[a.a_mat[tile.group] * a.ea_ld + row] : 0;
       const bool acc_ok = mbar_wait(&accbar, (unsigned)it & 1u, &abort_sh);
       // uniform over the epilogue group (also publishes the column metadata written above)
       if (!epi_all(acc_ok && !abort_sh)) {

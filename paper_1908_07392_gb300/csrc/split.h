@@ -40,6 +40,8 @@ struct SplitTables {
 struct SplitArgs {
   int M, Kpad, out_mode;        // out_mode 0: double-float slot (float2), 1: FP64 overwrite, 2: FP64 accumulate
   int nrt;                      // row tiles of 128 per operator matrix
+  int ea_ld;                    // rows per matrix in the row-exponent array (>= M: a launch may use the
+                                // leading M rows of its operators)
   const slice_t* A;             // tiled slices (SplitTable)
   const int* ea;
   const slice_t* B;             // sliced vectors [v][S][Kpad]

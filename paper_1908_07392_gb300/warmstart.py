@@ -16,7 +16,7 @@ import time
 
 import numpy as np
 
-from . import BIE, VP_PREC_FP64, VolumePotential, WarmStartNet, bie_stokeslets
+from . import BIE, VP_PREC_FP64, VolumePotential, WarmStartNet, bie_stokeslets, vp_layer_create, vp_layer_eval, vp_layer_free
 from . import inputs as I
 
 
@@ -141,17 +141,18 @@ def guess(bie, net, scale, mus, G, n):
     return ext, False, ratio
 
 
-def evaluate(bie, nets, mus, G, test_idx, tol, rhs=None):
+def evaluate(bie, nets, mus, G, test_idx, tol, rhs=None, post=None):
     """GMRES iterations and solve times from each initial guess on the held-out steps: cold, previous
     density, extrapolation through the last 3, 4 and 5 densities, and for every (name -> (net, scale))
     in nets the network's guess ("name") and its correction as an augmentation direction
     ("name_aug"). With rhs (n -> (g_n, ms)), the right-hand side is recomputed per step and its time
-    added to every method."""
+    added to every method; with post (mu -> ms), the step's velocity is formed from each solution and
+    its time added as well."""
     import torch
     names = ["cold", "previous", "extrapolation", "cubic", "quartic"]
     for nm in nets:
         names += [nm, nm + "_aug"]
-    res = {k: {"iters": [], "ms": []} for k in names}
+    res = {k: {"iters": [], "ms": [], "post_ms": []} for k in names}
     kept = {nm: 0 for nm in nets}
     ratios = {nm: [] for nm in nets}
     # one untimed pass through every path first (library and torch kernels load on first use)
@@ -171,8 +172,11 @@ def evaluate(bie, nets, mus, G, test_idx, tol, rhs=None):
         torch.cuda.synchronize()
         if not rr <= 10 * tol:
             raise RuntimeError(f"GMRES ({name}) did not reach the tolerance ({rr:.2e})")
+        solve_s = time.perf_counter() - t0
+        t_post = post(mu) if post is not None else 0.0
         res[name]["iters"].append(it)
-        res[name]["ms"].append(1000 * (time.perf_counter() - t0 + extra_s) + t_rhs)
+        res[name]["ms"].append(1000 * (solve_s + extra_s) + t_rhs + t_post)
+        res[name]["post_ms"].append(t_post)
 
     for n in test_idx:
         g, t_rhs = (G[n], 0.0) if rhs is None else rhs(n)
@@ -195,7 +199,7 @@ def evaluate(bie, nets, mus, G, test_idx, tol, rhs=None):
             torch.cuda.synchronize()
             solve(nm + "_aug", ext, time.perf_counter() - t0, t_rhs, aug=d)
     out = {k: {"mean_iters": float(np.mean(v["iters"])), "max_iters": int(np.max(v["iters"])),
-               "mean_ms": float(np.mean(v["ms"]))} for k, v in res.items()}
+               "mean_ms": float(np.mean(v["ms"])), "velocity_ms": float(np.mean(v["post_ms"]))} for k, v in res.items()}
     for nm in nets:
         out[nm]["kept_fraction"] = kept[nm] / max(1, len(test_idx))
         out[nm]["residual_ratio_vs_extrapolation"] = float(np.exp(np.mean(np.log(ratios[nm]))))
@@ -279,6 +283,10 @@ class StepProblem:
         self.bxy = bie.nodes[0:2].contiguous()
         self.u = torch.empty(self.vp.N, dtype=torch.float64, device="cuda")
         self.gradu = torch.empty(2, self.vp.N, dtype=torch.float64, device="cuda")
+        # the homogeneous part at the volume nodes: the double layer of the boundary density
+        self.layer = vp_layer_create(self.vp.tree, bie.nodes[0:5].cpu().numpy())
+        self.uh = torch.empty(2, self.vp.N, dtype=torch.float64, device="cuda")
+        self.vel = torch.empty(2, self.vp.N, dtype=torch.float64, device="cuda")
 
     def rhs(self, t):
         """g at time t (device [2N], interleaved per node) and the time of the volume part (ms)."""
@@ -296,7 +304,21 @@ class StepProblem:
         e1.synchronize()
         return g, e0.elapsed_time(e1)
 
+    def velocity(self, mu):
+        """The step's velocity at every volume node, u = u^P + u^H (Sec. 2.2): u^P = (dPsi/dy, -dPsi/dx)
+        from the last rhs() and u^H = D[mu] by the layer potential on the tree; returns the time (ms)."""
+        import torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        vp_layer_eval(self.layer, mu, self.uh)
+        self.vel[0] = self.gradu[1] + self.uh[0]
+        self.vel[1] = self.uh[1] - self.gradu[0]
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
     def close(self):
+        vp_layer_free(self.layer)
         self.vp.close()
 
 
@@ -333,7 +355,7 @@ def step_experiment(wl, n_panels=256, n_train=2000, n_test=200, tol=1e-11, preci
             if log:
                 log(f"training: {t_train:.1f} s, loss {scale['losses'][0]:.3e} -> {np.mean(scale['losses'][-20:]):.3e}")
             test_idx = np.arange(3 + n_train, steps)
-            ev = evaluate(bie, nets, mus, G, test_idx, tol, rhs=lambda n: prob.rhs(float(times[n])))
+            ev = evaluate(bie, nets, mus, G, test_idx, tol, rhs=lambda n: prob.rhs(float(times[n])), post=prob.velocity)
         finally:
             for net, _ in nets.values():
                 net.close()
