@@ -1099,7 +1099,9 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
       TRY(cudaGetLastError());
     } else if (st.kind == 6) {
       const DevPt& d = tr->pts[st.index];
-      const int rc = launch_pt_apply(d.rows, d.rb, d.bs, d.inst, d.n_inst, tr->d_perm, bufs_c[BUF_F], d.A,
+      // slots of split-precision trees hold double-float values; multipole coefficients are FP64
+      const int df = T->precision == VP_PREC_SPLIT && d.dst != BUF_MP;
+      const int rc = launch_pt_apply(d.rows, d.rb, d.bs, df, d.inst, d.n_inst, tr->d_perm, bufs_c[BUF_F], d.A,
                                      bufs[d.dst], s);
       if (rc) return rc;
     } else if (st.kind == 3) {

@@ -128,9 +128,9 @@ __global__ void __launch_bounds__(256) k_pt_near(double alpha, int p, const doub
 
 constexpr int kApplyThreads = 256, kApplyRows = 4, kApplyChunk = 1024;
 
-__global__ void __launch_bounds__(kApplyThreads) k_pt_apply(int rows, int rb, long long bs, const PtInst* inst,
-                                                             const int* perm, const double* mu, const double* A,
-                                                             double* Y) {
+__global__ void __launch_bounds__(kApplyThreads) k_pt_apply(int rows, int rb, long long bs, int df,
+                                                             const PtInst* inst, const int* perm, const double* mu,
+                                                             const double* A, double* Y) {
   __shared__ double xs[kApplyChunk];
   const PtInst I = inst[blockIdx.x];
   const int K = 2 * I.ns;
@@ -157,7 +157,14 @@ __global__ void __launch_bounds__(kApplyThreads) k_pt_apply(int rows, int rb, lo
   for (int q = 0; q < kApplyRows; ++q) {
     const int r = threadIdx.x + q * kApplyThreads;
     if (r >= rows) break;
-    Y[I.dst + (long long)(r / rb) * bs + r % rb] = acc[q];
+    const long long o = I.dst + (long long)(r / rb) * bs + r % rb;
+    if (df) {
+      // double-float slot (the contribution slots of split-precision trees): high and low fp32 parts
+      const float h = __double2float_rn(acc[q]);
+      reinterpret_cast<float2*>(Y)[o] = make_float2(h, __double2float_rn(acc[q] - (double)h));
+    } else {
+      Y[o] = acc[q];
+    }
   }
 }
 
@@ -182,11 +189,11 @@ int launch_pt_near(double alpha, int p, const double* xi, const PtInst* inst, in
   return VP_OK;
 }
 
-int launch_pt_apply(int rows, int rb, long long bs, const PtInst* inst, int n_inst, const int* perm,
+int launch_pt_apply(int rows, int rb, long long bs, int df, const PtInst* inst, int n_inst, const int* perm,
                     const double* mu, const double* A, double* Y, cudaStream_t s) {
   if (n_inst <= 0) return VP_OK;
   if (rows > kApplyThreads * kApplyRows || rb <= 0) return VP_ERR_ARG;
-  k_pt_apply<<<(unsigned)n_inst, kApplyThreads, 0, s>>>(rows, rb, bs, inst, perm, mu, A, Y);
+  k_pt_apply<<<(unsigned)n_inst, kApplyThreads, 0, s>>>(rows, rb, bs, df, inst, perm, mu, A, Y);
   TRY(cudaGetLastError());
   return VP_OK;
 }

@@ -35,8 +35,9 @@ int launch_pt_coeffs(int kind, double alpha, int P, const PtInst* inst, int n_in
 int launch_pt_near(double alpha, int p, const double* xi, const PtInst* inst, int n_inst, int max_ns,
                    PtSources src, double* A, cudaStream_t s);
 // Y[dst + (row / rb) bs + row % rb] = sum over columns of A times the density (mu interleaved
-// (mu_x, mu_y) per source), one block per instance.
-int launch_pt_apply(int rows, int rb, long long bs, const PtInst* inst, int n_inst, const int* perm,
+// (mu_x, mu_y) per source), one block per instance; df != 0 writes double-float (two fp32) values,
+// the slot format of split-precision trees, into the 8-byte elements of Y.
+int launch_pt_apply(int rows, int rb, long long bs, int df, const PtInst* inst, int n_inst, const int* perm,
                     const double* mu, const double* A, double* Y, cudaStream_t s);
 
 }  // namespace vp
