@@ -355,6 +355,110 @@ def batched_pair(args, V, local, world):
             "split_speedup_vs_fp64": sv / fv}
 
 
+def timed_steps(fn, steps, warmup, flush, stream):
+    """Milliseconds of each of `steps` calls of fn (CUDA events on `stream`, L2 flushed before each)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    out = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream); fn(); e1.record(stream); e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def layer_and_periodic(args, V):
+    """The two other paths to the velocity, measured beside the headline:
+    * the layer potential u^H = D[mu] at every node of the coupled-step tree (uniform depth 7, p = 16,
+      4.19M nodes, alpha = sqrt(Re/dt) = 316, split-precision tables) from the GMRES density of 256 x 16
+      boundary nodes, with its error against the exterior-stokeslet exact solution inside the star;
+    * the periodic particular solution by FFT (u and grad u) on a 4096^2 grid of the same box, with its
+      error against a manufactured exact solution."""
+    import numpy as np
+    import torch
+    from paper_1908_07392_gb300 import inputs as I
+    steps, warmup = max(3, min(args.steps, 10)), 3
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    wl = I.step_workload(seed=5)
+    b = V.BIE(wl.alpha, R=1.0, A=0.3, k=5, phase=wl.phi, n_panels=256)
+    vp = layer = None
+    try:
+        src, f = I.moving_stokeslets(5)(0.0)
+        S = torch.tensor(src, device="cuda"); Fs = torch.tensor(f, device="cuda")
+        g = V.bie_stokeslets(wl.alpha, S, Fs, b.nodes[0:2].contiguous()).t().contiguous().reshape(-1)
+        mu, it, rr = b.solve(g, None, 1e-13)
+        t0 = time.perf_counter()
+        vp = V.VolumePotential(I.KERNEL_MBIHARMONIC, wl.alpha, wl.p, wl.tree, precision=V.VP_PREC_SPLIT)
+        layer = V.vp_layer_create(vp.tree, b.nodes[0:5].cpu().numpy())
+        setup_s = time.perf_counter() - t0
+        u = torch.empty(2, vp.N, dtype=torch.float64, device="cuda")
+        ms = timed_steps(lambda: V.vp_layer_eval(layer, mu, u), steps, warmup, flush, stream)
+        xy = vp.nodes()
+        ue = V.bie_stokeslets(wl.alpha, S, Fs, xy).cpu().numpy()
+        X, Y = xy[0].cpu().numpy(), xy[1].cpu().numpy()
+        inside = np.hypot(X, Y) < 1.0 + 0.3 * np.cos(5 * np.arctan2(Y, X) + wl.phi) - 0.05
+        uu = u.cpu().numpy()
+        err = max(float(np.abs(uu[a][inside] - ue[a][inside]).max() / np.abs(ue[:, inside]).max()) for a in range(2))
+        flush.zero_(); torch.cuda.synchronize()
+        launches = V.vp_layer_steps(layer, mu, u)
+        kinds = {0: "fp64 gemm", 1: "fp64 reduce", 2: "memset", 3: "slice", 4: "split gemm", 5: "df reduce",
+                 6: "point operator"}
+        top = sorted(launches, key=lambda x: -x["ms"])[:6]
+        med = statistics.median(ms)
+        out["layer_potential"] = {
+            "workload": "coupled-step tree: uniform depth 7, p = 16, box [-1.5,1.5]^2, alpha 316, split tables; "
+                        "4096 boundary nodes (256 panels x 16), GMRES density for exterior stokeslets",
+            "value": vp.N / (med / 1e3), "unit": "nodes/s", "ms_per_eval": med, "steps": steps, "setup_s": setup_s,
+            "gmres_iterations": it,
+            "rel_err_vs_exact_inside": err, "inside_nodes": int(inside.sum()),
+            "launches": len(launches), "in_order_ms": sum(x["ms"] for x in launches),
+            "top_launches": [{"ms": round(x["ms"], 4), "kind": kinds.get(x["kind"], "?"),
+                              "stage": V.STAGE_NAMES[x["stage"]], "gflop": round(x["flops"] / 1e9, 3),
+                              "gbytes": round(x["bytes"] / 1e9, 3)} for x in top]}
+    finally:
+        if layer:
+            V.vp_layer_free(layer)
+        if vp is not None:
+            vp.close()
+        b.close()
+    # periodic FFT solution: manufactured divergence-free velocity with a pressure gradient added
+    n, L, alpha = 4096, 3.0, 316.0
+    x = torch.arange(n, dtype=torch.float64, device="cuda") * (L / n)
+    Yg, Xg = torch.meshgrid(x, x, indexing="ij")
+    w = 2 * np.pi / L
+    a_, b_ = 7 * w, 5 * w
+    s1, c1, s2, c2 = torch.sin(a_ * Xg + 0.3), torch.cos(a_ * Xg + 0.3), torch.sin(b_ * Yg - 0.7), torch.cos(b_ * Yg - 0.7)
+    u_ex = torch.stack([-b_ * s1 * s2, -a_ * c1 * c2])
+    F = (alpha ** 2 + a_ * a_ + b_ * b_) * u_ex + torch.stack([-w * torch.sin(w * Xg) * torch.sin(3 * w * Yg),
+                                                            3 * w * torch.cos(w * Xg) * torch.cos(3 * w * Yg)])
+    F = F.contiguous()
+    P = V.PeriodicStokes(alpha, n, L)
+    try:
+        u = torch.empty(2, n, n, dtype=torch.float64, device="cuda")
+        gu = torch.empty(2, 2, n, n, dtype=torch.float64, device="cuda")
+        ms = timed_steps(lambda: P(F, u, gu), steps, warmup, flush, stream)
+        err = float((u - u_ex).abs().max() / u_ex.abs().max())
+    finally:
+        P.close()
+    med = statistics.median(ms)
+    flops = 4 * 10.0 * n * n * np.log2(n)  # one forward and three inverse complex 2-D transforms, radix 2
+    fp64_peak = N_SM * 2070.0e6 * FP64_FLOPS_PER_CLK_PER_SM / 1e12
+    out["periodic_fft"] = {
+        "workload": f"periodic modified Stokes velocity and gradient on a {n}^2 grid, box side 3, alpha 316",
+        "value": n * n / (med / 1e3), "unit": "grid points/s", "ms_per_eval": med, "steps": steps,
+        "rel_err_vs_manufactured": err,
+        "roofline": {"bound": "alu", "kernel": "FP64 radix-2 butterflies (shared memory)",
+                     "achieved": flops / (med / 1e3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": flops / (med / 1e3) / 1e12 / fp64_peak,
+                     "flops_note": "10 n^2 log2 n per complex 2-D transform, 4 transforms"}}
+    return out
+
+
 def run_batched(args):
     import torch
     import paper_1908_07392_gb300 as V
@@ -635,6 +739,8 @@ def main():
     plain = measure(args, V, w, V.VP_PREC_FP64, world, local, False) if args.precision == "both" else None
     # the batched workload (64 trees in one CUDA graph), split and FP64, in the same run
     batched = None if (args.no_batched or args.precision != "both") else batched_pair(args, V, local, world)
+    # the layer potential and the periodic FFT solution
+    extras = None if (args.no_batched or args.precision != "both" or world > 1) else layer_and_periodic(args, V)
     errs = {}
     if cpu is not None:
         idx, vals = cpu_sample.last
@@ -679,6 +785,8 @@ def main():
             line["split_speedup_vs_fp64"] = head["value"] / plain["value"]
         if batched is not None:
             line["batched"] = batched
+        if extras is not None:
+            line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
