@@ -279,6 +279,16 @@ int vp_plan_pairs(int n_leaves, const int32_t* level, const int32_t* ix, const i
  *  must not overlap on the GPU; like vp_eval, the near part runs on `stream` while the far-field
  *  chain runs on a side stream joined back before the output.
  * vp_layer_steps -- vp_layer_eval with every launch timed in order, as vp_eval_steps.
+ * vp_layer_near_star -- accurate values at the nodes close to the boundary (Sec. 4.2 and 4.4: the
+ *  plain panel rule loses accuracy within about a panel length), for a layer whose points are the panel
+ *  nodes of the star r(t) = R + A cos(k t + phase), t in [0, 2 pi) counter-clockwise, in n_panels equal
+ *  parameter panels of 16 Gauss-Legendre nodes, panel after panel (as bie_nodes lists them; VP_ERR_ARG
+ *  otherwise). Every (node, panel) pair closer than `dist` panel lengths (0 < dist <= 8; the paper tests
+ *  1.2) gets the panel's contribution with the density interpolated by the panel's Lagrange basis,
+ *  integrated on the exact curve by 20-point Gauss-Legendre on pieces graded dyadically toward the
+ *  closest point, in place of the plain rule. The weight differences are built here on the device
+ *  (FP64) and vp_layer_eval adds them after the tree sum. *n_pairs (may be NULL) receives the number of
+ *  pairs. At most once per layer; synchronises `stream`.
  * Errors: VP_ERR_ARG, VP_ERR_OOM, VP_ERR_CUDA.
  */
 typedef struct vp_layer_s* vp_layer;
@@ -286,6 +296,8 @@ int vp_layer_create(vp_tree tree, int n_src, const double* src, void* stream, vp
 int vp_layer_eval(vp_layer layer, const double* mu, double* u, void* stream);
 int vp_layer_steps(vp_layer layer, const double* mu, double* u, void* stream, int cap, int* n_steps, float* ms,
                    int* info, double* flops, double* bytes);
+int vp_layer_near_star(vp_layer layer, double R, double A, int k, double phase, int n_panels, double dist,
+                       void* stream, int64_t* n_pairs);
 void vp_layer_free(vp_layer layer);
 
 /*
@@ -334,14 +346,19 @@ int vp_eval_static(vp_tree tree, const double* f, double* u, double* gradu, void
 
 /*
  * Engines of the split-precision contractions (trees on VP_PREC_SPLIT tables):
- *  0  warp-level mma.sync m16n8k16 (bf16 slices in, four fp32 accumulators in registers);
+ *  0  warp-level mma.sync m16n8k16 (bf16 slices in, four fp32 accumulators in registers), tiles of
+ *     128 rows x 64 columns;
  *  1  tcgen05.mma kind::f16 (bf16 slices) issued by one thread of a persistent CTA per SM, four fp32
- *     accumulators in tensor memory; operator slices staged by TMA, gathered source columns by
- *     cp.async, a 4-stage ring handed over through mbarriers; every wait bounded.
- * Both compute the same exact slice sums. vp_tree_set_engine sets one engine for every launch of
+ *     accumulators in tensor memory, tiles of 128 x 128; operator slices staged by one bulk copy per
+ *     K step, gathered source columns by cp.async, a 4-stage ring handed over through mbarriers;
+ *     every wait bounded;
+ *  2  mma.sync as engine 0 on tiles of 64 x 32 (four times the blocks: for small launches whose
+ *     time is the latency of a few tiles).
+ * All compute the same exact slice sums. vp_tree_set_engine sets one engine for every launch of
  * the tree (VP_ERR_ARG for other values). vp_autotune times each split-precision launch of one
- * evaluation of `f` with both engines on `stream`, keeps the faster per launch, evaluates once more
- * into u, gradu with the choice, and, if *n_tcgen05 is given, reports how many launches use engine 1.
+ * evaluation of `f` with every engine (tile shape) on `stream`, keeps the fastest per launch shape,
+ * evaluates once more into u, gradu with the choice, and, if *n_tcgen05 is given, reports how many
+ * launches use engine 1.
  * With cache_path (may be NULL) the choices are read from / appended to a text file keyed by
  * (p, P, channels, operator, rows, padded K, tiles). Trees on FP64 tables are left unchanged.
  * vp_device_status reads and clears the device flag a bounded wait sets when it gives up:

@@ -91,3 +91,63 @@ def layer_potential(alpha, src, mu, tx, ty, chunk=2048):
         for a in range(2):
             u[a, sl] = (D[a, 0] * (mu[:, 0] * w)[None, :] + D[a, 1] * (mu[:, 1] * w)[None, :]).sum(axis=1)
     return u
+
+
+def lagrange(x_nodes, t):
+    """Lagrange basis of the nodes at points t (barycentric form): L[len(t)][len(x_nodes)]."""
+    x_nodes = np.asarray(x_nodes, float)
+    t = np.atleast_1d(np.asarray(t, float))
+    w = np.array([1.0 / np.prod([x_nodes[j] - x_nodes[m] for m in range(x_nodes.size) if m != j])
+                  for j in range(x_nodes.size)])
+    L = np.empty((t.size, x_nodes.size))
+    for i, ti in enumerate(t):
+        d = ti - x_nodes
+        hit = np.flatnonzero(d == 0.0)
+        if hit.size:
+            L[i] = 0.0
+            L[i, hit[0]] = 1.0
+        else:
+            v = w / d
+            L[i] = v / v.sum()
+    return L
+
+
+def layer_potential_accurate(alpha, geom, n_panels, mu, tx, ty, near=1.2, q=16):
+    """u [2][M] at targets of the double layer with the density given at the panel nodes (mu [n][2],
+    panel order) and interpolated on each panel by its Lagrange basis in the parameter: panels farther
+    than `near` panel lengths from a target by the panel rule, nearer ones by adaptive quadrature
+    (scipy quad, split at the closest parameter) of the interpolated density on the exact curve."""
+    import scipy.integrate as si
+    R, A, k, ph = geom["R"], geom["A"], geom["k"], geom["phase"]
+    x, y, nx, ny, w, t = star_nodes(R, A, k, ph, n_panels, q)
+    mu = np.asarray(mu, float).reshape(-1, 2)
+    g, _ = np.polynomial.legendre.leggauss(q)
+    h = 2 * np.pi / n_panels
+    plen = w.reshape(n_panels, q).sum(axis=1)
+    tx = np.atleast_1d(np.asarray(tx, float)); ty = np.atleast_1d(np.asarray(ty, float))
+    u = np.zeros((2, tx.size))
+    for m in range(tx.size):
+        for pnl in range(n_panels):
+            sl = slice(pnl * q, (pnl + 1) * q)
+            ta = pnl * h
+            ts = np.linspace(ta, ta + h, 129)
+            (sx, sy), _ = star(R, A, k, ph, ts)
+            dist = np.hypot(sx - tx[m], sy - ty[m])
+            if dist.min() >= near * plen[pnl]:
+                D = kernel(alpha, tx[m] - x[sl], ty[m] - y[sl], nx[sl], ny[sl])
+                for a in range(2):
+                    u[a, m] += np.sum((D[a, 0] * mu[sl, 0] + D[a, 1] * mu[sl, 1]) * w[sl])
+                continue
+            t0 = ts[int(np.argmin(dist))]
+
+            def f(s, a):
+                (yx, yy), (dx, dy) = star(R, A, k, ph, np.array([s]))
+                sp_ = np.hypot(dx, dy)
+                D = kernel(alpha, tx[m] - yx, ty[m] - yy, -dy / sp_, dx / sp_)[:, :, 0]
+                L = lagrange(g, 2 * (s - ta) / h - 1)[0]
+                return float((D[a, 0] * (L @ mu[sl, 0]) + D[a, 1] * (L @ mu[sl, 1])) * sp_[0])
+
+            pts = [t0] if ta < t0 < ta + h else None
+            for a in range(2):
+                u[a, m] += si.quad(f, ta, ta + h, args=(a,), points=pts, epsabs=1e-15, epsrel=1e-13, limit=500)[0]
+    return u

@@ -102,6 +102,7 @@ def load_library():
                                    ctypes.POINTER(c_double)]
     lib.vp_layer_free.argtypes = [c_void_p]
     lib.vp_layer_free.restype = None
+    lib.vp_layer_near_star.argtypes = [c_void_p, c_double, c_double, c_int, c_double, c_int, c_double, c_void_p, i64p]
     lib.vp_periodic_create.argtypes = [c_double, c_int, c_double, c_void_p, ctypes.POINTER(c_void_p)]
     lib.vp_periodic_eval.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.vp_periodic_free.argtypes = [c_void_p]
@@ -124,7 +125,7 @@ def exported_symbols():
     """Names declared in include/vp.h (the ABI surface)."""
     return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_tree_interp", "vp_special", "vp_eval", "vp_eval_host",
             "vp_eval_timed", "vp_tree_stats", "vp_tree_bytes", "vp_eval_steps", "vp_layer_create", "vp_layer_eval",
-            "vp_layer_steps", "vp_layer_free", "vp_periodic_create", "vp_periodic_eval", "vp_periodic_free", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
+            "vp_layer_steps", "vp_layer_free", "vp_layer_near_star", "vp_periodic_create", "vp_periodic_eval", "vp_periodic_free", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
             "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status", "vp_selftest_timeout",
             "bie_create", "bie_free", "bie_size", "bie_nodes", "bie_apply", "bie_solve", "bie_solve_aug", "bie_eval",
@@ -134,6 +135,7 @@ def exported_symbols():
 
 ENGINE_MMA_SYNC = 0
 ENGINE_TCGEN05 = 1
+ENGINE_MMA_SMALL = 2
 
 
 def vp_tree_set_engine(tree: int, engine: int):
@@ -338,6 +340,15 @@ class PeriodicStokes:
         if getattr(self, "handle", None):
             load_library().vp_periodic_free(ctypes.c_void_p(self.handle))
             self.handle = None
+
+
+def vp_layer_near_star(layer: int, R, A, k, phase, n_panels, dist=1.2, stream=None) -> int:
+    """Near-boundary corrections for a layer whose points are the star's panel nodes; returns the pair count."""
+    n = ctypes.c_int64()
+    _check(load_library().vp_layer_near_star(ctypes.c_void_p(layer), float(R), float(A), int(k), float(phase),
+                                             int(n_panels), float(dist), _stream_ptr(stream), ctypes.byref(n)),
+           "vp_layer_near_star")
+    return n.value
 
 
 def vp_layer_free(layer: int):

@@ -27,6 +27,7 @@
 
 #include "layer.h"
 #include "plan.h"
+#include "special.cuh"
 #include "split.h"
 #include "vp_internal.h"
 
@@ -279,8 +280,8 @@ struct DevReduce {
 struct DevSplit {
   SplitArgs args;
   int table, vec, dst;
-  const SplitTile* tiles[2];    // tile lists of the two engines
-  int n_tiles[2];
+  const SplitTile* tiles[kEngines];  // tile lists of the engines
+  int n_tiles[kEngines];
   int engine = kEngineMmaSync;  // chosen per launch (vp_tree_set_engine, vp_autotune)
 };
 
@@ -306,9 +307,18 @@ struct DevPt {
   double* A = nullptr;
 };
 
+// Near-boundary corrections of a layer program: per corrected node its (node, panel) pairs (CSR) and
+// the weight differences (layer.h).
+struct DevNear {
+  long long n_nodes = 0, n_pairs = 0;
+  long long *node = nullptr, *ptr = nullptr;
+  int* panel = nullptr;
+  double* dW = nullptr;
+};
+
 struct Step {
   int kind;   // 0 gemm, 1 reduce, 2 memset mp, 3 slice vectors, 4 split gemm, 5 double-float reduce,
-              // 6 point-source operator
+              // 6 point-source operator, 7 near-boundary correction of the output
   int index;
   int stage;  // VP_STAGE_* for timing
   double flops = 0.0;  // algorithmic floating-point operations of the step
@@ -351,6 +361,7 @@ struct vp_tree_s {
   // the source permutation they read the density through
   long long mp_elems = 0;
   std::vector<vp::DevPt> pts;
+  std::vector<vp::DevNear> nears;
   int* d_perm = nullptr;
   // overlap of the near field with the far-field chain (vp_eval): the chain runs on `side`, a
   // high-priority stream, the near field on the caller's stream; events fork and join them
@@ -435,7 +446,7 @@ int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
   const long long mat_elems = g.mat_elems ? g.mat_elems : (long long)g.M * g.lda;
   const long long vec_len = g.split_vec == 0 ? T->n : (g.split_vec == 1 ? T->C : T->E);  // families 0-2
   std::vector<long long> a_mat, src_vec, dst_off;
-  std::vector<SplitTile> tiles[2];
+  std::vector<SplitTile> tiles[kEngines];
   size_t i = 0;
   while (i < g.entries.size()) {
     size_t j = i;
@@ -450,24 +461,26 @@ int upload_split(vp_tree_s* tr, HostGemm& g, cudaStream_t s) {
     const int ncols = (int)(j - i);
     // the row tiles of one column block are consecutive, so the CTAs that run them at the same time
     // share the block's gathered source columns in L2
-    for (int en = 0; en < 2; ++en)
+    for (int en = 0; en < kEngines; ++en)
       for (int c0 = 0; c0 < ncols; c0 += kSplitBN[en])
-        for (int m0 = 0; m0 < g.M; m0 += kSplitBM)
+        for (int m0 = 0; m0 < g.M; m0 += kSplitBMe[en])
           tiles[en].push_back({grp, m0, col_begin + c0, std::min(kSplitBN[en], ncols - c0)});
     i = j;
   }
   DevSplit d{};
   d.args.M = g.M; d.args.Kpad = split_kpad(g.K); d.args.out_mode = g.out_mode;
-  SplitTile *dt0, *dt1; long long *da, *ds, *dd;
+  long long *da, *ds, *dd;
   int rc;
-  if ((rc = dev_upload(tr, tiles[0], &dt0, s))) return rc;
-  if ((rc = dev_upload(tr, tiles[1], &dt1, s))) return rc;
+  for (int en = 0; en < kEngines; ++en) {
+    SplitTile* dt = nullptr;
+    if ((rc = dev_upload(tr, tiles[en], &dt, s))) return rc;
+    d.tiles[en] = dt;
+    d.n_tiles[en] = (int)tiles[en].size();
+  }
   if ((rc = dev_upload(tr, a_mat, &da, s))) return rc;
   if ((rc = dev_upload(tr, src_vec, &ds, s))) return rc;
   if ((rc = dev_upload(tr, dst_off, &dd, s))) return rc;
   d.args.a_mat = da; d.args.src_vec = ds; d.args.dst_off = dd;
-  d.tiles[0] = dt0; d.tiles[1] = dt1;
-  d.n_tiles[0] = (int)tiles[0].size(); d.n_tiles[1] = (int)tiles[1].size();
   d.table = g.table; d.vec = g.split_vec; d.dst = g.dst;
   // algorithmic bytes: sliced operators (S bf16 slices + a row exponent) and sliced source vectors
   // (S slices + an exponent) read once, outputs written once (8 bytes: a double-float slot or FP64)
@@ -1097,6 +1110,10 @@ int run_steps(vp_tree_s* tr, const double* f, double* u, double* g, cudaStream_t
       if (a.M > 4 * threads) return VP_ERR_ARG;  // at most 4 rows per thread (3 p^2 <= 768)
       k_reduce<<<d.n_dst, threads, 0, s>>>(a);
       TRY(cudaGetLastError());
+    } else if (st.kind == 7) {
+      const DevNear& d = tr->nears[st.index];
+      const int rc = launch_near_apply(d.n_nodes, d.node, d.ptr, d.panel, d.dW, bufs_c[BUF_F], tr->N, u, s);
+      if (rc) return rc;
     } else if (st.kind == 6) {
       const DevPt& d = tr->pts[st.index];
       // slots of split-precision trees hold double-float values; multipole coefficients are FP64
@@ -1383,7 +1400,7 @@ extern "C" const char* vp_strerror(int code) {
 // Engine selection and autotuning of the split-precision contractions.
 
 extern "C" int vp_tree_set_engine(vp_tree tree, int engine) {
-  if (!tree || (engine != 0 && engine != 1)) return VP_ERR_ARG;
+  if (!tree || engine < 0 || engine >= kEngines) return VP_ERR_ARG;
   for (auto& d : tree->splits) d.engine = engine;
   return VP_OK;
 }
@@ -1472,22 +1489,26 @@ extern "C" int vp_autotune(vp_tree tree, const double* f, double* u, double* gra
     if (choice[k] < 0) need = true;
   }
   if (need) {
-    std::vector<float> t0, t1;
-    int rc = time_split_launches(tree, f, u, gradu, kEngineMmaSync, s, t0);
-    if (rc == VP_OK) rc = time_split_launches(tree, f, u, gradu, kEngineTcgen05, s, t1);
+    std::vector<float> tt[kEngines];
+    int rc = VP_OK;
+    for (int en = 0; en < kEngines && rc == VP_OK; ++en) rc = time_split_launches(tree, f, u, gradu, en, s, tt[en]);
     if (rc == VP_OK) rc = vp_device_status();
     if (rc != VP_OK) {
       vp_tree_set_engine(tree, kEngineMmaSync);
       return rc;
     }
-    // one decision per key: the engine with the smaller total time over the launches sharing it
+    // one decision per key: the engine (tile shape) with the smallest total time over the launches
+    // sharing it
     for (int k = 0; k < ns; ++k) {
       if (choice[k] >= 0) continue;
       const std::string key = key_of(tree->splits[k]);
-      double a0 = 0.0, a1 = 0.0;
+      double tot[kEngines] = {0.0, 0.0, 0.0};
       for (int m = 0; m < ns; ++m)
-        if (key_of(tree->splits[m]) == key) { a0 += t0[m]; a1 += t1[m]; }
-      const int c = (a1 < a0) ? kEngineTcgen05 : kEngineMmaSync;
+        if (key_of(tree->splits[m]) == key)
+          for (int en = 0; en < kEngines; ++en) tot[en] += tt[en][m];
+      int c = 0;
+      for (int en = 1; en < kEngines; ++en)
+        if (tot[en] < tot[c]) c = en;
       for (int m = 0; m < ns; ++m)
         if (choice[m] < 0 && key_of(tree->splits[m]) == key) choice[m] = c;
     }
@@ -1656,6 +1677,11 @@ extern "C" int vp_eval_batched(int n_trees, const vp_tree* trees, const double* 
 struct vp_layer_s {
   vp_tree_s* prog = nullptr;  // the step program over the tree's boxes (owns its buffers)
   int n_src = 0;
+  std::vector<double> src;                 // host copy of the points [5][n_src]
+  std::vector<int> lv, ix, iy;             // the tree's leaves
+  int p = 0;
+  double cx = 0.0, cy = 0.0, side = 0.0;
+  bool corrected = false;
 };
 
 extern "C" int vp_layer_create(vp_tree tree, int n_src, const double* src, void* stream, vp_layer* out) {
@@ -1736,7 +1762,142 @@ extern "C" int vp_layer_create(vp_tree tree, int n_src, const double* src, void*
   if (!L) return fail(VP_ERR_OOM);
   L->prog = pr.release();
   L->n_src = n_src;
+  L->src.assign(src, src + 5 * (size_t)n_src);
+  L->lv = tree->h_lv; L->ix = tree->h_ix; L->iy = tree->h_iy;
+  L->p = T->p; L->cx = tree->cx; L->cy = tree->cy; L->side = T->side;
   *out = L.release();
+  return VP_OK;
+}
+
+namespace {
+// Point and derivative of the star r(t) = R + A cos(k t + phase) (host).
+void star_host(const StarGeom& g, double t, double& x, double& y, double& dx, double& dy) {
+  const double c = std::cos(t), s = std::sin(t);
+  const double r = g.R + g.A * std::cos(g.k * t + g.phase), dr = -g.A * g.k * std::sin(g.k * t + g.phase);
+  x = r * c; y = r * s;
+  dx = dr * c - r * s; dy = dr * s + r * c;
+}
+}  // namespace
+
+extern "C" int vp_layer_near_star(vp_layer layer, double R, double A, int k, double phase, int n_panels,
+                                  double dist, void* stream, int64_t* n_pairs_out) {
+  if (!layer || !(R > 0.0) || !(A >= 0.0) || A >= R || k < 0 || n_panels < 1 || !(dist > 0.0) || dist > 8.0)
+    return VP_ERR_ARG;
+  if (layer->corrected) return VP_ERR_ARG;  // one correction per layer
+  constexpr int Q = kNearQ;
+  if ((long long)n_panels * Q != layer->n_src) return VP_ERR_ARG;
+  const StarGeom g{R, A, phase, k, n_panels};
+  const double hp = 2.0 * kPi / n_panels;
+  std::vector<double> gx(Q), gw(Q);
+  gauss_legendre_host(Q, gx.data(), gw.data());
+  // the layer's points must be the star's panel nodes, in panel order
+  const int n = layer->n_src;
+  const double* S = layer->src.data();
+  std::vector<double> plen(n_panels, 0.0);
+  for (int pnl = 0; pnl < n_panels; ++pnl)
+    for (int q = 0; q < Q; ++q) {
+      const int j = pnl * Q + q;
+      double x, y, dx, dy;
+      star_host(g, pnl * hp + 0.5 * hp * (1.0 + gx[q]), x, y, dx, dy);
+      const double sp = std::hypot(dx, dy);
+      if (std::fabs(S[j] - x) > 1e-12 * (R + A) || std::fabs(S[n + j] - y) > 1e-12 * (R + A) ||
+          std::fabs(S[2 * n + j] + dy / sp) > 1e-10 || std::fabs(S[3 * n + j] - dx / sp) > 1e-10)
+        return VP_ERR_ARG;
+      plen[pnl] += S[4 * n + j];
+    }
+  // node coordinates of the tree (host) and the pairs within dist panel lengths of a panel
+  const int p = layer->p, nn = p * p;
+  std::vector<double> xi(p), wi(p);
+  gauss_legendre_host(p, xi.data(), wi.data());
+  const double x0 = layer->cx - 0.5 * layer->side, y0 = layer->cy - 0.5 * layer->side;
+  const int nl = (int)layer->lv.size();
+  struct HP { long long node; int panel; double t0, d, x, y; };
+  std::vector<HP> hp_pairs;
+  constexpr int kSamp = 64;
+  for (int pnl = 0; pnl < n_panels; ++pnl) {
+    const double ta = pnl * hp, reach = dist * plen[pnl];
+    double bx0 = 1e300, bx1 = -1e300, by0 = 1e300, by1 = -1e300;
+    std::vector<double> sx(kSamp + 1), sy(kSamp + 1);
+    for (int m = 0; m <= kSamp; ++m) {
+      double dx, dy;
+      star_host(g, ta + hp * m / kSamp, sx[m], sy[m], dx, dy);
+      bx0 = std::min(bx0, sx[m]); bx1 = std::max(bx1, sx[m]);
+      by0 = std::min(by0, sy[m]); by1 = std::max(by1, sy[m]);
+    }
+    bx0 -= reach; bx1 += reach; by0 -= reach; by1 += reach;
+    for (int lf = 0; lf < nl; ++lf) {
+      const double h = layer->side / (double)(1ll << layer->lv[lf]);
+      const double lx = x0 + layer->ix[lf] * h, ly = y0 + layer->iy[lf] * h;
+      if (lx > bx1 || lx + h < bx0 || ly > by1 || ly + h < by0) continue;
+      for (int t = 0; t < nn; ++t) {
+        const double x = lx + 0.5 * (1.0 + xi[t % p]) * h, y = ly + 0.5 * (1.0 + xi[t / p]) * h;
+        if (x < bx0 || x > bx1 || y < by0 || y > by1) continue;
+        int mb = 0;
+        double best = 1e300;
+        for (int m = 0; m <= kSamp; ++m) {
+          const double d2 = (sx[m] - x) * (sx[m] - x) + (sy[m] - y) * (sy[m] - y);
+          if (d2 < best) { best = d2; mb = m; }
+        }
+        // Newton on (y(t) - x) . y'(t) = 0 from the nearest sample, kept inside the panel
+        double t0 = ta + hp * mb / kSamp;
+        for (int it = 0; it < 30; ++it) {
+          const double e = 1e-7 * hp;
+          double yx, yy, dx, dy, ya, yb, dxa, dya;
+          star_host(g, t0, yx, yy, dx, dy);
+          const double f0 = (yx - x) * dx + (yy - y) * dy;
+          star_host(g, t0 + e, ya, yb, dxa, dya);
+          const double f1 = (ya - x) * dxa + (yb - y) * dya;
+          const double fp = (f1 - f0) / e;
+          if (!(fp > 0.0)) break;
+          const double tn = std::min(ta + hp, std::max(ta, t0 - f0 / fp));
+          const bool done = std::fabs(tn - t0) < 1e-15 * hp;
+          t0 = tn;
+          if (done) break;
+        }
+        double yx, yy, dx, dy;
+        star_host(g, t0, yx, yy, dx, dy);
+        const double d = std::hypot(yx - x, yy - y);
+        if (d < reach) hp_pairs.push_back({(long long)lf * nn + t, pnl, t0, d, x, y});
+      }
+    }
+  }
+  std::stable_sort(hp_pairs.begin(), hp_pairs.end(), [](const HP& a, const HP& b) { return a.node < b.node; });
+  std::vector<NearPair> pairs(hp_pairs.size());
+  std::vector<long long> node, ptr;
+  std::vector<int> panel(hp_pairs.size());
+  for (size_t i = 0; i < hp_pairs.size(); ++i) {
+    pairs[i] = {hp_pairs[i].x, hp_pairs[i].y, hp_pairs[i].t0, hp_pairs[i].d, hp_pairs[i].panel, 0};
+    panel[i] = hp_pairs[i].panel;
+    if (i == 0 || hp_pairs[i].node != hp_pairs[i - 1].node) { node.push_back(hp_pairs[i].node); ptr.push_back((long long)i); }
+  }
+  ptr.push_back((long long)hp_pairs.size());
+  if (n_pairs_out) *n_pairs_out = (int64_t)hp_pairs.size();
+  if (hp_pairs.empty()) { layer->corrected = true; return VP_OK; }
+  vp_tree_s* tr = layer->prog;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DevNear d;
+  d.n_nodes = (long long)node.size();
+  d.n_pairs = (long long)pairs.size();
+  NearPair* dp = nullptr;
+  int rc;
+  if ((rc = dev_upload(tr, pairs, &dp, s))) return rc;
+  if ((rc = dev_upload(tr, node, &d.node, s))) return rc;
+  if ((rc = dev_upload(tr, ptr, &d.ptr, s))) return rc;
+  if ((rc = dev_upload(tr, panel, &d.panel, s))) return rc;
+  void* w = nullptr;
+  TRY(cudaMalloc(&w, (size_t)d.n_pairs * Q * 4 * sizeof(double)));
+  tr->allocs.push_back(w);
+  d.dW = static_cast<double*>(w);
+  if ((rc = launch_near_weights(tr->T->alpha, g, dp, d.n_pairs, d.dW, s))) return rc;
+  const double fl = 2.0 * 16.0 * (double)d.n_pairs * Q;
+  const double by = 8.0 * (double)d.n_pairs * Q * 4 + 16.0 * (double)d.n_nodes;
+  tr->steps.push_back({7, (int)tr->nears.size(), VP_STAGE_OUTPUT, fl, by});
+  tr->flops[VP_STAGE_OUTPUT] += fl;
+  tr->bytes[VP_STAGE_OUTPUT] += by;
+  tr->nears.push_back(d);
+  layer->corrected = true;
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) { set_last_cuda(e); return VP_ERR_CUDA; }
   return VP_OK;
 }
 

@@ -23,6 +23,9 @@
 // rounding and needs no per-moment formulas.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "layer.h"
 #include "special.cuh"
 #include "stokes.cuh"
@@ -194,6 +197,193 @@ int launch_pt_apply(int rows, int rb, long long bs, int df, const PtInst* inst, 
   if (n_inst <= 0) return VP_OK;
   if (rows > kApplyThreads * kApplyRows || rb <= 0) return VP_ERR_ARG;
   k_pt_apply<<<(unsigned)n_inst, kApplyThreads, 0, s>>>(rows, rb, bs, df, inst, perm, mu, A, Y);
+  TRY(cudaGetLastError());
+  return VP_OK;
+}
+
+}  // namespace vp
+
+// ------------------------------------------------------------------------------------------------
+// Near-boundary correction (Sec. 4.2, 4.4: the plain panel rule fails for targets within about a panel
+// length of the panel; the paper corrects those point-panel pairs with precomputed weights).
+//
+// For a pair (target x, panel [ta, tb] of the parameter), the panel's contribution with the density
+// interpolated by the panel's Lagrange basis in t,
+//     int_panel D(x - y(t)) l_j(t) |y'(t)| dt,   j = 0 .. 15,
+// is integrated on the exact curve by Gauss-Legendre (20 points) on pieces graded dyadically toward
+// t0, the parameter of the closest point: each piece lies about its own length away from x, so the
+// near-singular integrand is resolved at every distance, down to pieces shorter than half the distance
+// d. The kernel is evaluated directly (App. B closed form, App. C series for small alpha r), so the
+// panel needs no subdivision for large alpha h (the kernel-split quadrature of Sec. 4.2 needs alpha h
+// <= 4.5, Eq. alpha_h_crit, because its split parts grow like e^(alpha r)). The plain weight
+// D(x - y_j) w_j, which the tree sum already contains, is subtracted.
+namespace vp {
+namespace {
+
+constexpr int kGQ = 20;        // Gauss-Legendre points per graded piece
+constexpr int kMaxGrade = 44;  // dyadic levels per side at most
+__constant__ double c_g20x[kGQ], c_g20w[kGQ], c_g16x[kNearQ], c_g16w[kNearQ], c_bw16n[kNearQ];
+
+__device__ inline void star_point(const StarGeom& g, double t, double& x, double& y, double& sp) {
+  double s, c, s5, c5;
+  sincos(t, &s, &c);
+  sincos(g.k * t + g.phase, &s5, &c5);
+  const double r = g.R + g.A * c5, dr = -g.A * g.k * s5;
+  x = r * c;
+  y = r * s;
+  const double dx = dr * c - r * s, dy = dr * s + r * c;
+  sp = sqrt(dx * dx + dy * dy);
+}
+
+__device__ inline void star_normal(const StarGeom& g, double t, double& nx, double& ny) {
+  double s, c, s5, c5;
+  sincos(t, &s, &c);
+  sincos(g.k * t + g.phase, &s5, &c5);
+  const double r = g.R + g.A * c5, dr = -g.A * g.k * s5;
+  const double dx = dr * c - r * s, dy = dr * s + r * c;
+  const double sp = sqrt(dx * dx + dy * dy);
+  nx = -dy / sp;  // counter-clockwise: the interior is on the left of the tangent
+  ny = dx / sp;
+}
+
+// One 64-thread block per pair: in rounds of 64 quadrature points each thread evaluates the kernel
+// and the 16 Lagrange basis values at one point into shared memory, then thread (j, ab) accumulates
+// its weight over the round.
+__global__ void __launch_bounds__(64) k_near_weights(double alpha, StarGeom g, const NearPair* pairs, double* dW) {
+  __shared__ double Dq[64][4], Lq[64][kNearQ];
+  const NearPair P = pairs[blockIdx.x];
+  const double hp = 2.0 * kPi / g.n_panels;
+  const double ta = P.panel * hp, tb = ta + hp;
+  // graded pieces: left of t0 (toward t0 from ta) and right (toward t0 from tb); the length of
+  // the last piece is below half the distance (arc length ~ parameter length times the speed)
+  double x0, y0, sp0;
+  star_point(g, P.t0, x0, y0, sp0);
+  const double dmin = fmax(P.d, 1e-14 * hp * sp0);
+  int nl = 0, nr = 0;
+  if (P.t0 - ta > 0.0) {
+    double len = P.t0 - ta;
+    while (nl < kMaxGrade && len * sp0 > 0.5 * dmin) { len *= 0.5; ++nl; }
+  }
+  if (tb - P.t0 > 0.0) {
+    double len = tb - P.t0;
+    while (nr < kMaxGrade && len * sp0 > 0.5 * dmin) { len *= 0.5; ++nr; }
+  }
+  // pieces: left k = 0..nl-1: [t0 - L/2^k, t0 - L/2^(k+1)], then [t0 - L/2^nl, t0]; right likewise
+  const int n_left = (P.t0 - ta > 0.0) ? nl + 1 : 0, n_right = (tb - P.t0 > 0.0) ? nr + 1 : 0;
+  const int n_pts = (n_left + n_right) * kGQ;
+  const int j = threadIdx.x >> 2, ab = threadIdx.x & 3;
+  double acc = 0.0;
+  for (int q0 = 0; q0 < n_pts; q0 += 64) {
+    const int q = q0 + threadIdx.x;
+    __syncthreads();
+    if (q < n_pts) {
+      const int piece = q / kGQ, m = q % kGQ;
+      double a, b;
+      if (piece < n_left) {
+        const double L = P.t0 - ta;
+        a = (piece < nl) ? P.t0 - L * ldexp(1.0, -piece) : P.t0 - L * ldexp(1.0, -nl);
+        b = (piece < nl) ? P.t0 - L * ldexp(1.0, -piece - 1) : P.t0;
+      } else {
+        const int k = piece - n_left;
+        const double L = tb - P.t0;
+        a = (k < nr) ? P.t0 + L * ldexp(1.0, -k - 1) : P.t0;
+        b = (k < nr) ? P.t0 + L * ldexp(1.0, -k) : P.t0 + L * ldexp(1.0, -nr);
+      }
+      const double t = 0.5 * (a + b) + 0.5 * (b - a) * c_g20x[m];
+      const double wq = 0.5 * (b - a) * c_g20w[m];
+      double yx, yy, sp, nx, ny;
+      star_point(g, t, yx, yy, sp);
+      star_normal(g, t, nx, ny);
+      double D[4] = {0.0, 0.0, 0.0, 0.0};
+      const double rx = P.x - yx, ry = P.y - yy;
+      if (rx != 0.0 || ry != 0.0) dl_kernel(alpha, rx, ry, nx, ny, D);
+      for (int c = 0; c < 4; ++c) Dq[threadIdx.x][c] = D[c] * wq * sp;
+      // Lagrange basis of the panel's nodes at t (barycentric, reference coordinate in [-1, 1])
+      const double tau = 2.0 * (t - ta) / hp - 1.0;
+      double den = 0.0;
+      int hit = -1;
+      for (int i = 0; i < kNearQ; ++i) {
+        const double dd = tau - c_g16x[i];
+        if (dd == 0.0) hit = i;
+        else den += c_bw16n[i] / dd;
+      }
+      for (int i = 0; i < kNearQ; ++i)
+        Lq[threadIdx.x][i] = (hit >= 0) ? (i == hit ? 1.0 : 0.0) : (c_bw16n[i] / (tau - c_g16x[i])) / den;
+    } else {
+      for (int c = 0; c < 4; ++c) Dq[threadIdx.x][c] = 0.0;
+      for (int i = 0; i < kNearQ; ++i) Lq[threadIdx.x][i] = 0.0;
+    }
+    __syncthreads();
+    const int nq = min(64, n_pts - q0);
+    for (int qq = 0; qq < nq; ++qq) acc = fma(Dq[qq][ab], Lq[qq][j], acc);
+  }
+  // minus the plain weight of node j: D(x - y_j) w_j
+  {
+    const double t = ta + 0.5 * hp * (1.0 + c_g16x[j]);
+    double yx, yy, sp, nx, ny;
+    star_point(g, t, yx, yy, sp);
+    star_normal(g, t, nx, ny);
+    double D[4] = {0.0, 0.0, 0.0, 0.0};
+    const double rx = P.x - yx, ry = P.y - yy;
+    if (rx != 0.0 || ry != 0.0) dl_kernel(alpha, rx, ry, nx, ny, D);
+    acc -= D[ab] * 0.5 * hp * c_g16w[j] * sp;
+  }
+  dW[(size_t)blockIdx.x * (kNearQ * 4) + j * 4 + ab] = acc;
+}
+
+__global__ void k_near_apply(long long n_nodes, const long long* node, const long long* ptr, const int* panel,
+                             const double* dW, const double* mu, long long N, double* u) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= n_nodes) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (long long p = ptr[k]; p < ptr[k + 1]; ++p) {
+    const double* w = dW + p * (kNearQ * 4);
+    const long long base = (long long)panel[p] * kNearQ;
+    for (int j = 0; j < kNearQ; ++j) {
+      const double m0 = mu[2 * (base + j)], m1 = mu[2 * (base + j) + 1];
+      s0 = fma(w[4 * j + 0], m0, fma(w[4 * j + 1], m1, s0));
+      s1 = fma(w[4 * j + 2], m0, fma(w[4 * j + 3], m1, s1));
+    }
+  }
+  const long long o = node[k];
+  u[o] += s0;
+  u[N + o] += s1;
+}
+
+}  // namespace
+
+int launch_near_weights(double alpha, StarGeom g, const NearPair* pairs, long long n_pairs, double* dW,
+                        cudaStream_t s) {
+  if (n_pairs <= 0) return VP_OK;
+  static bool rules = false;
+  if (!rules) {
+    std::vector<double> x20(kGQ), w20(kGQ), x16(kNearQ), w16(kNearQ), bw(kNearQ);
+    gauss_legendre_host(kGQ, x20.data(), w20.data());
+    gauss_legendre_host(kNearQ, x16.data(), w16.data());
+    for (int i = 0; i < kNearQ; ++i) {
+      double prod = 1.0;
+      for (int m = 0; m < kNearQ; ++m) if (m != i) prod *= x16[i] - x16[m];
+      bw[i] = 1.0 / prod;
+    }
+    TRY(cudaMemcpyToSymbol(c_g20x, x20.data(), kGQ * sizeof(double)));
+    TRY(cudaMemcpyToSymbol(c_g20w, w20.data(), kGQ * sizeof(double)));
+    TRY(cudaMemcpyToSymbol(c_g16x, x16.data(), kNearQ * sizeof(double)));
+    TRY(cudaMemcpyToSymbol(c_g16w, w16.data(), kNearQ * sizeof(double)));
+    TRY(cudaMemcpyToSymbol(c_bw16n, bw.data(), kNearQ * sizeof(double)));
+    rules = true;
+  }
+  for (long long p0 = 0; p0 < n_pairs; p0 += 1 << 30) {
+    const long long np = std::min<long long>(n_pairs - p0, 1 << 30);
+    k_near_weights<<<(unsigned)np, 64, 0, s>>>(alpha, g, pairs + p0, dW + p0 * kNearQ * 4);
+    TRY(cudaGetLastError());
+  }
+  return VP_OK;
+}
+
+int launch_near_apply(long long n_nodes, const long long* node, const long long* ptr, const int* panel,
+                      const double* dW, const double* mu, long long N, double* u, cudaStream_t s) {
+  if (n_nodes <= 0) return VP_OK;
+  k_near_apply<<<(unsigned)((n_nodes + 127) / 128), 128, 0, s>>>(n_nodes, node, ptr, panel, dW, mu, N, u);
   TRY(cudaGetLastError());
   return VP_OK;
 }

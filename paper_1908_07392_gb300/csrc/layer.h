@@ -41,3 +41,23 @@ int launch_pt_apply(int rows, int rb, long long bs, int df, const PtInst* inst, 
                     const double* mu, const double* A, double* Y, cudaStream_t s);
 
 }  // namespace vp
+
+namespace vp {
+
+// Near-boundary correction of the layer potential for sources that are the panel nodes of the star
+// r(t) = R + A cos(k t + phase) (equal parameter panels of kNearQ Gauss-Legendre nodes).
+constexpr int kNearQ = 16;
+struct StarGeom { double R, A, phase; int k, n_panels; };
+// One (target node, panel) pair: target coordinates, the panel, and the parameter of the closest
+// point of the panel to the target with the distance.
+struct NearPair { double x, y, t0, d; int panel, pad; };
+// dW[pair][j][a][b] (j < kNearQ) = graded-quadrature weight of node j of the panel for velocity
+// component a and density component b, minus the plain Gauss-Legendre weight of that node.
+int launch_near_weights(double alpha, StarGeom g, const NearPair* pairs, long long n_pairs, double* dW,
+                        cudaStream_t s);
+// u[a][node] += sum over the node's pairs of dW times the density of the pair's panel nodes; node k of the
+// list is `node[k]`, its pairs ptr[k] .. ptr[k+1].
+int launch_near_apply(long long n_nodes, const long long* node, const long long* ptr, const int* panel,
+                      const double* dW, const double* mu, long long N, double* u, cudaStream_t s);
+
+}  // namespace vp

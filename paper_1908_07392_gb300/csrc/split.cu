@@ -180,7 +180,6 @@ __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n
 
 // ------------------------------------------------------------------ engine 0: mma.sync
 
-constexpr int kMBN = kSplitBN[kEngineMmaSync];          // 64
 constexpr int kMKC = 32, kMPitch = kMKC + 8;             // K chunk and shared row pitch (elements)
 
 __device__ inline void ldmatrix_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
@@ -198,35 +197,38 @@ __device__ inline void mma16816(float* c, const unsigned* a, const unsigned* b) 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-template <int S>
-__global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
+// Tile BM x BN, warps of 32 x 32 (BM/32 along M, BN/32 along N), K in chunks of 32, double buffered.
+template <int S, int BM, int BN>
+__global__ void __launch_bounds__(BM * BN / 32) k_split_gemm(SplitArgs a) {
+  constexpr int NT = BM * BN / 32, WM = BM / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   slice_t* As = reinterpret_cast<slice_t*>(smem_raw);                  // [2][S][BM][pitch]
-  slice_t* Bs = As + 2 * S * kSplitBM * kMPitch;                        // [2][S][BN][pitch]
+  slice_t* Bs = As + 2 * S * BM * kMPitch;                              // [2][S][BN][pitch]
   const SplitTile tile = a.tiles[blockIdx.x];
   const long long mat = a.a_mat[tile.group];
-  // this tile's rows in the tiled operator layout: [K step][slice][chunk][128 rows][8]
-  const slice_t* Ag = a.A + (mat * a.nrt + (tile.m0 >> 7)) * (long long)(a.Kpad / 16) * S * 2048;
+  // this tile's rows in the tiled operator layout: [K step][slice][chunk][128 rows][8], rows from
+  // m0 % 128 within the table tile
+  const slice_t* Ag = a.A + (mat * a.nrt + (tile.m0 >> 7)) * (long long)(a.Kpad / 16) * S * 2048 + (tile.m0 & 127) * 8;
   const int* ea = a.ea + mat * a.ea_ld;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp & 3, wn = warp >> 2;  // 4 warps along M (32 rows), 2 along N (32 columns)
+  const int wm = warp % WM, wn = warp / WM;  // WM warps along M (32 rows), BN/32 along N (32 columns)
   const int gid = lane >> 2, tig = lane & 3;
 
   auto load_chunk = [&](int buf, int k0) {
-    for (int e = tid; e < S * kSplitBM * 4; e += 256) {
-      const int sl = e / (kSplitBM * 4), rem = e % (kSplitBM * 4);
-      const int c = rem >> 7, r = rem & 127;  // K chunk of 8 (0..3 within the 32), row
+    for (int e = tid; e < S * BM * 4; e += NT) {
+      const int sl = e / (BM * 4), rem = e % (BM * 4);
+      const int c = rem / BM, r = rem % BM;  // K chunk of 8 (0..3 within the 32), row
       const slice_t* src = Ag + ((long long)(((k0 >> 4) + (c >> 1)) * S + sl) * 2 + (c & 1)) * 1024 + r * 8;
-      cp_async16(As + ((buf * S + sl) * kSplitBM + r) * kMPitch + c * 8, src, true);  // padding rows are zeros
+      cp_async16(As + ((buf * S + sl) * BM + r) * kMPitch + c * 8, src, true);  // padding rows are zeros
     }
     // one column's two K steps of 16 are 4 S contiguous 16-byte chunks (step, slice, half)
-    for (int e = tid; e < S * kMBN * 4; e += 256) {
+    for (int e = tid; e < S * BN * 4; e += NT) {
       const int col = e / (S * 4), w = e % (S * 4);
       const int ks = w / (S * 2), sl = (w >> 1) % S, h = w & 1;
       const bool ok = col < tile.ncol;
       const long long v = ok ? a.src_vec[tile.col0 + col] : 0;
       const slice_t* src = a.B + v * S * (long long)a.Kpad + (k0 >> 4) * (S * 16) + w * 8;
-      cp_async16(Bs + ((buf * S + sl) * kMBN + col) * kMPitch + ks * 16 + h * 8, src, ok);
+      cp_async16(Bs + ((buf * S + sl) * BN + col) * kMPitch + ks * 16 + h * 8, src, ok);
     }
     cp_async_commit();
   };
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
       unsigned bf[S][4][2];
 #pragma unroll
       for (int j = 0; j < S; ++j) {
-        const slice_t* Bb = Bs + ((buf * S + j) * kMBN + wn * 32) * kMPitch;
+        const slice_t* Bb = Bs + ((buf * S + j) * BN + wn * 32) * kMPitch;
 #pragma unroll
         for (int nt2 = 0; nt2 < 2; ++nt2) {
           unsigned r0, r1, r2, r3;
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
       }
 #pragma unroll
       for (int i = 0; i < S; ++i) {
-        const slice_t* Ab = As + ((buf * S + i) * kSplitBM + wm * 32) * kMPitch;
+        const slice_t* Ab = As + ((buf * S + i) * BM + wm * 32) * kMPitch;
         unsigned af[2][4];
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(256) k_split_gemm(SplitArgs a) {
     }
 }
 
-size_t mma_smem_bytes(int S) { return (size_t)2 * S * (kSplitBM + kMBN) * kMPitch * sizeof(slice_t); }
+size_t mma_smem_bytes(int S, int BM, int BN) { return (size_t)2 * S * (BM + BN) * kMPitch * sizeof(slice_t); }
 
 // ------------------------------------------------------------------ engine 1: tcgen05
 //
@@ -791,8 +793,10 @@ int prepare_split_launch() {
   TRY(cudaGetDevice(&dev));
   static bool done[64] = {false};
   if (dev >= 0 && dev < 64 && done[dev]) return VP_OK;
-  TRY(cudaFuncSetAttribute(k_split_gemm<kSplitSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)mma_smem_bytes(kSplitSlices)));
+  TRY(cudaFuncSetAttribute(k_split_gemm<kSplitSlices, 128, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)mma_smem_bytes(kSplitSlices, 128, 64)));
+  TRY(cudaFuncSetAttribute(k_split_gemm<kSplitSlices, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)mma_smem_bytes(kSplitSlices, 64, 32)));
   TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_bytes(kSplitSlices)));
   int sms = 0;
@@ -830,8 +834,10 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engin
     const int grid = (short_ctas || n_tiles < g_num_sms) ? n_tiles : g_num_sms;
     k_split_gemm_tc<kSplitSlices><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(a, n_tiles);
   }
+  else if (engine == kEngineMmaSmall)
+    k_split_gemm<kSplitSlices, 64, 32><<<n_tiles, 64, mma_smem_bytes(kSplitSlices, 64, 32), s>>>(a);
   else
-    k_split_gemm<kSplitSlices><<<n_tiles, 256, mma_smem_bytes(kSplitSlices), s>>>(a);
+    k_split_gemm<kSplitSlices, 128, 64><<<n_tiles, 256, mma_smem_bytes(kSplitSlices, 128, 64), s>>>(a);
   TRY(cudaGetLastError());
   return VP_OK;
 }

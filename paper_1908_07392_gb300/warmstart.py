@@ -16,7 +16,8 @@ import time
 
 import numpy as np
 
-from . import BIE, VP_PREC_FP64, VolumePotential, WarmStartNet, bie_stokeslets, vp_layer_create, vp_layer_eval, vp_layer_free
+from . import (BIE, VP_PREC_FP64, VolumePotential, WarmStartNet, bie_stokeslets, vp_autotune, vp_layer_create,
+               vp_layer_eval, vp_layer_free, vp_layer_near_star)
 from . import inputs as I
 
 
@@ -283,8 +284,13 @@ class StepProblem:
         self.bxy = bie.nodes[0:2].contiguous()
         self.u = torch.empty(self.vp.N, dtype=torch.float64, device="cuda")
         self.gradu = torch.empty(2, self.vp.N, dtype=torch.float64, device="cuda")
-        # the homogeneous part at the volume nodes: the double layer of the boundary density
+        if precision != VP_PREC_FP64:
+            # contraction engine per launch shape, chosen once for this tree
+            vp_autotune(self.vp.tree, self.wl.source(self.X, self.Y, 0.0), self.u, self.gradu)
+        # the homogeneous part at the volume nodes: the double layer of the boundary density, with the
+        # near-boundary correction for the nodes within 1.2 panel lengths of the boundary
         self.layer = vp_layer_create(self.vp.tree, bie.nodes[0:5].cpu().numpy())
+        self.near_pairs = vp_layer_near_star(self.layer, 1.0, 0.3, 5, wl.phi, bie.N // 16, 1.2)
         self.uh = torch.empty(2, self.vp.N, dtype=torch.float64, device="cuda")
         self.vel = torch.empty(2, self.vp.N, dtype=torch.float64, device="cuda")
 

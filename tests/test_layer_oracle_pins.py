@@ -89,3 +89,39 @@ def test_velocity_is_divergence_free():
     dvdy = uy[1] @ cw
     grad = max(abs(dudx), abs(dvdy), abs(ux[1] @ cw), abs(uy[0] @ cw))
     assert abs(dudx + dvdy) < 1e-9 * grad, (dudx, dvdy)
+
+
+def test_lagrange_reproduces_polynomials():
+    g, _ = np.polynomial.legendre.leggauss(16)
+    t = np.concatenate([np.linspace(-1.0, 1.0, 41), g[:3]])  # also exactly at nodes
+    L = LO.lagrange(g, t)
+    for deg in (0, 5, 15):
+        c = np.random.default_rng(deg).standard_normal(deg + 1)
+        assert np.abs(L @ np.polynomial.polynomial.polyval(g, c) - np.polynomial.polynomial.polyval(t, c)).max() < 1e-12 * max(1.0, np.abs(c).sum())
+
+
+def test_accurate_sum_matches_panel_rule_away_from_the_boundary():
+    # at targets far from every panel both the accurate and the plain sums are the panel rule
+    alpha = 10.0
+    x, y, nx, ny, w, t = LO.star_nodes(n_panels=24, **STAR)
+    mu = density(t)
+    tx, ty = np.array([0.1, -0.3]), np.array([0.05, 0.2])
+    ua = LO.layer_potential_accurate(alpha, STAR, 24, mu, tx, ty, near=1.2)
+    up = LO.layer_potential(alpha, (x, y, nx, ny, w), mu, tx, ty)
+    assert np.abs(ua - up).max() < 1e-14 * np.abs(up).max()
+
+
+def test_accurate_sum_near_the_boundary_converges_with_panels():
+    # close to the boundary the plain rule fails; the accurate sum with the density given by a smooth
+    # function of t converges to the continuous integral as the panels are refined (spectrally)
+    alpha = 10.0
+    (bx, by), (dx, dy) = LO.star(STAR["R"], STAR["A"], STAR["k"], STAR["phase"], np.array([1.1]))
+    sp_ = np.hypot(dx, dy)
+    tx, ty = bx - 0.004 * (dy / sp_), by + 0.004 * (dx / sp_)  # inward normal step of 0.004
+    vals = []
+    for npnl in (20, 40):
+        x, y, nx, ny, w, t = LO.star_nodes(n_panels=npnl, **STAR)
+        vals.append(LO.layer_potential_accurate(alpha, STAR, npnl, density(t), tx, ty, near=1.2)[:, 0])
+        plain = LO.layer_potential(alpha, (x, y, nx, ny, w), density(t), tx, ty)[:, 0]
+    assert np.abs(vals[1] - vals[0]).max() < 1e-9 * np.abs(vals[1]).max()
+    assert np.abs(plain - vals[1]).max() > 1e-6 * np.abs(vals[1]).max()  # the plain rule is far off there
