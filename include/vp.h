@@ -319,6 +319,32 @@ int vp_periodic_eval(vp_periodic plan, const double* F, double* u, double* gradu
 void vp_periodic_free(vp_periodic plan);
 
 /*
+ * Semi-implicit spectral deferred correction time stepping (Sec. 3.3; Eqs. sisdc_initial,
+ * sisdc_formula, rhs_initial, rhs_correction, rhs_correction_integral) of the Navier-Stokes equations
+ * u_t + (u . grad) u = Laplacian u / Re - grad p, div u = 0 on a periodic box of side L, every implicit
+ * substep solved by the periodic modified Stokes solution above with alpha^2 = Re / dt. Order K in
+ * 1..4: K >= 2 takes K - 1 equal substeps of dt = Delta t / (K - 1) and K - 1 correction passes (K^2 - K
+ * solves per step; global order K); K = 1 is one IMEX Euler step (one solve). The nonlinear term
+ * (u . grad) u is formed pointwise on the grid from u and its Fourier gradient; the implicit term of a
+ * substep is recovered from its own equation (Laplacian u - Re grad p = alpha^2 u - F).
+ * vp_sdc_create -- Re > 0, Delta t > 0, order 1..4, n and L as vp_periodic_create (device memory:
+ *  about (2 K^2 + 12) n^2 doubles; synchronises `stream`).
+ * vp_sdc_set -- the state at the first time: u0 device [2][n][n], its gradient gradu0 [2][2][n][n]
+ *  (gradu0[a][m] = d u_a / d x_m) and its Laplacian lap0 [2][n][n] (the paper supplies Laplacian u at the
+ *  initial time, Sec. 3.3). Must precede vp_sdc_step.
+ * vp_sdc_step -- advances n_steps steps of Delta t, all on `stream` without host synchronisation.
+ * vp_sdc_get -- copies the current u [2][n][n] and its gradient [2][2][n][n] (device).
+ * Calls on one stepper must not overlap on the GPU.
+ * Errors: VP_ERR_ARG, VP_ERR_OOM, VP_ERR_CUDA.
+ */
+typedef struct vp_sdc_s* vp_sdc;
+int vp_sdc_create(double re, double dt, int order, int n, double side, void* stream, vp_sdc* out);
+int vp_sdc_set(vp_sdc sdc, const double* u0, const double* gradu0, const double* lap0, void* stream);
+int vp_sdc_step(vp_sdc sdc, int n_steps, void* stream);
+int vp_sdc_get(vp_sdc sdc, double* u, double* gradu, void* stream);
+void vp_sdc_free(vp_sdc sdc);
+
+/*
  * vp_eval_static -- vp_eval that allocates nothing.
  *
  * For callers that cannot call cudaMalloc (or any allocating routine) at the
@@ -353,12 +379,15 @@ int vp_eval_static(vp_tree tree, const double* f, double* u, double* gradu, void
  *     K step, gathered source columns by cp.async, a 4-stage ring handed over through mbarriers;
  *     every wait bounded;
  *  2  mma.sync as engine 0 on tiles of 64 x 32 (four times the blocks: for small launches whose
- *     time is the latency of a few tiles).
+ *     time is the latency of a few tiles);
+ *  3  tcgen05 as engine 1 on tiles of 128 x 64, with two sets of four accumulators in tensor
+ *     memory, so that the epilogue of one tile overlaps the MMAs of the next (for short K, where
+ *     draining the accumulators takes longer than filling them).
  * All compute the same exact slice sums. vp_tree_set_engine sets one engine for every launch of
  * the tree (VP_ERR_ARG for other values). vp_autotune times each split-precision launch of one
  * evaluation of `f` with every engine (tile shape) on `stream`, keeps the fastest per launch shape,
  * evaluates once more into u, gradu with the choice, and, if *n_tcgen05 is given, reports how many
- * launches use engine 1.
+ * launches use a tcgen05 engine (1 or 3).
  * With cache_path (may be NULL) the choices are read from / appended to a text file keyed by
  * (p, P, channels, operator, rows, padded K, tiles). Trees on FP64 tables are left unchanged.
  * vp_device_status reads and clears the device flag a bounded wait sets when it gives up:

@@ -107,6 +107,12 @@ def load_library():
     lib.vp_periodic_eval.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.vp_periodic_free.argtypes = [c_void_p]
     lib.vp_periodic_free.restype = None
+    lib.vp_sdc_create.argtypes = [c_double, c_double, c_int, c_int, c_double, c_void_p, ctypes.POINTER(c_void_p)]
+    lib.vp_sdc_set.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.vp_sdc_step.argtypes = [c_void_p, c_int, c_void_p]
+    lib.vp_sdc_get.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.vp_sdc_free.argtypes = [c_void_p]
+    lib.vp_sdc_free.restype = None
     lib.vp_eval_steps.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.POINTER(c_int),
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(c_int), ctypes.POINTER(c_double),
                                   ctypes.POINTER(c_double)]
@@ -125,7 +131,7 @@ def exported_symbols():
     """Names declared in include/vp.h (the ABI surface)."""
     return ["vp_tables_build", "vp_tree_upload", "vp_tree_size", "vp_tree_nodes", "vp_tree_interp", "vp_special", "vp_eval", "vp_eval_host",
             "vp_eval_timed", "vp_tree_stats", "vp_tree_bytes", "vp_eval_steps", "vp_layer_create", "vp_layer_eval",
-            "vp_layer_steps", "vp_layer_free", "vp_layer_near_star", "vp_periodic_create", "vp_periodic_eval", "vp_periodic_free", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
+            "vp_layer_steps", "vp_layer_free", "vp_layer_near_star", "vp_periodic_create", "vp_periodic_eval", "vp_periodic_free", "vp_sdc_create", "vp_sdc_set", "vp_sdc_step", "vp_sdc_get", "vp_sdc_free", "vp_tree_free", "vp_tables_free", "vp_strerror", "vp_plan_pairs",
             "vp_eval_static", "vp_batch_create", "vp_batch_run", "vp_batch_stats", "vp_batch_free",
             "vp_eval_batched", "vp_last_cuda_error", "vp_tree_set_engine", "vp_autotune", "vp_device_status", "vp_selftest_timeout",
             "bie_create", "bie_free", "bie_size", "bie_nodes", "bie_apply", "bie_solve", "bie_solve_aug", "bie_eval",
@@ -136,6 +142,7 @@ def exported_symbols():
 ENGINE_MMA_SYNC = 0
 ENGINE_TCGEN05 = 1
 ENGINE_MMA_SMALL = 2
+ENGINE_TCGEN05_N64 = 3
 
 
 def vp_tree_set_engine(tree: int, engine: int):
@@ -339,6 +346,41 @@ class PeriodicStokes:
     def close(self):
         if getattr(self, "handle", None):
             load_library().vp_periodic_free(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+
+class SISDC:
+    """Navier-Stokes time stepping on a periodic n x n grid of a box of side L by semi-implicit spectral
+    deferred correction of order 1..4, every substep a periodic modified Stokes solve (include/vp.h)."""
+
+    def __init__(self, re, dt, order, n, side, stream=None):
+        out = ctypes.c_void_p()
+        _check(load_library().vp_sdc_create(float(re), float(dt), int(order), int(n), float(side),
+                                            _stream_ptr(stream), ctypes.byref(out)), "vp_sdc_create")
+        self.handle, self.n, self.re, self.dt, self.order, self.side = out.value, n, re, dt, order, side
+
+    def set(self, u0, gradu0, lap0, stream=None):
+        """u0 [2, n, n], gradu0 [2, 2, n, n], lap0 [2, n, n]: device float64, contiguous."""
+        _check(load_library().vp_sdc_set(ctypes.c_void_p(self.handle), ctypes.c_void_p(u0.data_ptr()),
+                                         ctypes.c_void_p(gradu0.data_ptr()), ctypes.c_void_p(lap0.data_ptr()),
+                                         _stream_ptr(stream)), "vp_sdc_set")
+
+    def step(self, n_steps=1, stream=None):
+        _check(load_library().vp_sdc_step(ctypes.c_void_p(self.handle), int(n_steps), _stream_ptr(stream)),
+               "vp_sdc_step")
+
+    def get(self, u=None, gradu=None, stream=None):
+        import torch
+        n = self.n
+        u = torch.empty(2, n, n, dtype=torch.float64, device="cuda") if u is None else u
+        gradu = torch.empty(2, 2, n, n, dtype=torch.float64, device="cuda") if gradu is None else gradu
+        _check(load_library().vp_sdc_get(ctypes.c_void_p(self.handle), ctypes.c_void_p(u.data_ptr()),
+                                         ctypes.c_void_p(gradu.data_ptr()), _stream_ptr(stream)), "vp_sdc_get")
+        return u, gradu
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().vp_sdc_free(ctypes.c_void_p(self.handle))
             self.handle = None
 
 

@@ -1502,7 +1502,7 @@ extern "C" int vp_autotune(vp_tree tree, const double* f, double* u, double* gra
     for (int k = 0; k < ns; ++k) {
       if (choice[k] >= 0) continue;
       const std::string key = key_of(tree->splits[k]);
-      double tot[kEngines] = {0.0, 0.0, 0.0};
+      double tot[kEngines] = {};
       for (int m = 0; m < ns; ++m)
         if (key_of(tree->splits[m]) == key)
           for (int en = 0; en < kEngines; ++en) tot[en] += tt[en][m];
@@ -1528,7 +1528,10 @@ extern "C" int vp_autotune(vp_tree tree, const double* f, double* u, double* gra
     }
   }
   int ntc = 0;
-  for (int k = 0; k < ns; ++k) { tree->splits[k].engine = choice[k]; ntc += choice[k] == kEngineTcgen05; }
+  for (int k = 0; k < ns; ++k) {
+    tree->splits[k].engine = choice[k];
+    ntc += choice[k] == kEngineTcgen05 || choice[k] == kEngineTcgen05N64;
+  }
   if (n_tcgen05) *n_tcgen05 = ntc;
   // leave u, gradu holding a valid evaluation with the chosen engines
   return run_steps(tree, f, u, gradu, s);

@@ -331,23 +331,35 @@ __global__ void __launch_bounds__(64) k_near_weights(double alpha, StarGeom g, c
   dW[(size_t)blockIdx.x * (kNearQ * 4) + j * 4 + ab] = acc;
 }
 
+// One warp per corrected node: lane l takes entries l and l + 32 of each pair's 64 weights (node j =
+// e / 4, component pair e % 4), so a warp reads a pair's 512 bytes in two coalesced loads; the two
+// velocity components are reduced across the warp in a fixed order.
 __global__ void k_near_apply(long long n_nodes, const long long* node, const long long* ptr, const int* panel,
                              const double* dW, const double* mu, long long N, double* u) {
-  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long k = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (k >= n_nodes) return;
   double s0 = 0.0, s1 = 0.0;
   for (long long p = ptr[k]; p < ptr[k + 1]; ++p) {
     const double* w = dW + p * (kNearQ * 4);
     const long long base = (long long)panel[p] * kNearQ;
-    for (int j = 0; j < kNearQ; ++j) {
-      const double m0 = mu[2 * (base + j)], m1 = mu[2 * (base + j) + 1];
-      s0 = fma(w[4 * j + 0], m0, fma(w[4 * j + 1], m1, s0));
-      s1 = fma(w[4 * j + 2], m0, fma(w[4 * j + 3], m1, s1));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = lane + 32 * h, j = e >> 2, c = e & 3;
+      const double v = w[e] * mu[2 * (base + j) + (c & 1)];
+      if (c < 2) s0 += v; else s1 += v;
     }
   }
-  const long long o = node[k];
-  u[o] += s0;
-  u[N + o] += s1;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if (lane == 0) {
+    const long long o = node[k];
+    u[o] += s0;
+    u[N + o] += s1;
+  }
 }
 
 }  // namespace
@@ -383,7 +395,7 @@ int launch_near_weights(double alpha, StarGeom g, const NearPair* pairs, long lo
 int launch_near_apply(long long n_nodes, const long long* node, const long long* ptr, const int* panel,
                       const double* dW, const double* mu, long long N, double* u, cudaStream_t s) {
   if (n_nodes <= 0) return VP_OK;
-  k_near_apply<<<(unsigned)((n_nodes + 127) / 128), 128, 0, s>>>(n_nodes, node, ptr, panel, dW, mu, N, u);
+  k_near_apply<<<(unsigned)((n_nodes * 32 + 255) / 256), 256, 0, s>>>(n_nodes, node, ptr, panel, dW, mu, N, u);
   TRY(cudaGetLastError());
   return VP_OK;
 }

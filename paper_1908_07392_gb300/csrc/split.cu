@@ -146,9 +146,12 @@ __device__ inline void df_add(float& hi, float& lo, float x) {
 __device__ inline float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 __device__ inline double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
 
-// Store one output element: double-float (h, l) times 2^e, as a double-float slot or into FP64.
-// Scaling by a power of two is exact (ldexp only where 2^e itself is not a normal number).
-__device__ inline void store_out(const SplitArgs& a, long long dst, int row, float h, float l, int e) {
+// One output element: double-float (h, l) times 2^e, as a double-float slot (out_mode 0) or in
+// FP64 (out_mode 1 overwrites, 2 adds to `old`, the value the destination held before the launch).
+// Scaling by a power of two is exact (ldexp only where 2^e itself is not a normal number). Callers
+// with out_mode 2 read the old values of a group of outputs first, so that the reads of the group
+// are in flight together instead of one read-add-store chain per element.
+__device__ inline void store_out(const SplitArgs& a, long long dst, int row, float h, float l, int e, double old) {
   if (a.out_mode == 0) {
     float2 o;
     if (e >= -126 && e <= 127) {
@@ -163,8 +166,7 @@ __device__ inline void store_out(const SplitArgs& a, long long dst, int row, flo
   } else {
     const double hl = (double)h + (double)l;
     const double val = (e >= -1022 && e <= 1023) ? hl * pow2d(e) : ldexp(hl, e);
-    double* y = reinterpret_cast<double*>(a.Y) + dst + row;
-    *y = (a.out_mode == 2) ? *y + val : val;
+    reinterpret_cast<double*>(a.Y)[dst + row] = (a.out_mode == 2) ? old + val : val;
   }
 }
 
@@ -291,14 +293,32 @@ __global__ void __launch_bounds__(BM * BN / 32) k_split_gemm(SplitArgs a) {
   }
 
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt)
+  for (int nt = 0; nt < 4; ++nt) {
+    bool cok[2];
+    int eb[2];
+    long long dst[2];
 #pragma unroll
     for (int cc = 0; cc < 2; ++cc) {
       const int col = wn * 32 + nt * 8 + tig * 2 + cc;
-      if (col >= tile.ncol) continue;
-      const long long v = a.src_vec[tile.col0 + col];
-      const int eb = a.eb[v];
-      const long long dst = a.dst_off[tile.col0 + col];
+      cok[cc] = col < tile.ncol;
+      eb[cc] = cok[cc] ? a.eb[a.src_vec[tile.col0 + col]] : 0;
+      dst[cc] = cok[cc] ? a.dst_off[tile.col0 + col] : 0;
+    }
+    double old[2][2][2] = {};
+    if (a.out_mode == 2) {
+#pragma unroll
+      for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int rr = 0; rr < 2; ++rr) {
+            const int row = tile.m0 + wm * 32 + mt * 16 + gid + rr * 8;
+            if (cok[cc] && row < a.M) old[cc][mt][rr] = reinterpret_cast<const double*>(a.Y)[dst[cc] + row];
+          }
+    }
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      if (!cok[cc]) continue;
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -308,9 +328,10 @@ __global__ void __launch_bounds__(BM * BN / 32) k_split_gemm(SplitArgs a) {
           float h = 0.f, l = 0.f;
 #pragma unroll
           for (int w = 0; w < kAcc; ++w) df_add(h, l, acc[w][mt][nt][rr * 2 + cc]);
-          store_out(a, dst, row, h, l, ea[row] + eb);
+          store_out(a, dst[cc], row, h, l, ea[row] + eb[cc], old[cc][mt][rr]);
         }
     }
+  }
 }
 
 size_t mma_smem_bytes(int S, int BM, int BN) { return (size_t)2 * S * (BM + BN) * kMPitch * sizeof(slice_t); }
@@ -346,14 +367,23 @@ constexpr int kTcProducers = 256;                 // warps 0-7
 constexpr int kTcEpilogue = 256;                  // warps 8-15
 constexpr int kTcMmaWarp = (kTcProducers + kTcEpilogue) / 32;  // warp 16
 constexpr int kTcThreads = kTcProducers + kTcEpilogue + 32;
-constexpr int kTcN = kSplitBN[kEngineTcgen05];   // 128
 constexpr int kTcKC = 16;                         // K per stage
 constexpr int kTcStages = 4;
-constexpr int kTcCols = kAcc * kTcN;              // 512 tensor-memory columns
+constexpr int kTcCols = 512;                      // tensor-memory columns allocated per CTA
 constexpr int kTcA = kSplitBM * kTcKC;            // elements per A slice tile
-constexpr int kTcB = kTcN * kTcKC;                // elements per B slice tile
-static_assert(kTcCols <= 512, "tensor memory holds 512 columns");
-static_assert(kSplitBM == 128 && kTcN == 128 && kTcProducers == 256 && kTcEpilogue == 256, "thread mapping");
+static_assert(kSplitBN[kEngineTcgen05] == 128 && kSplitBN[kEngineTcgen05N64] == 64, "tcgen05 tile widths");
+static_assert(kSplitBM == 128 && kTcProducers == 256 && kTcEpilogue == 256, "thread mapping");
+
+// Tile width BN (columns) of a tcgen05 engine: the four accumulators take 4 BN tensor-memory
+// columns, so at BN = 64 two sets fit and the MMAs of a tile run while the epilogue drains the
+// previous one (at BN = 128 the epilogue and the next tile's MMAs alternate).
+template <int BN>
+struct TcShape {
+  static constexpr int kB = BN * kTcKC;           // elements per B slice tile
+  static constexpr int kAccCols = kAcc * BN;      // tensor-memory columns of one accumulator set
+  static constexpr int kBufs = kTcCols / kAccCols;
+  static_assert(kBufs >= 1 && kBufs * kAccCols == kTcCols, "accumulator sets fill tensor memory");
+};
 
 __device__ inline unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -398,15 +428,15 @@ __device__ inline void umma_f16(unsigned d_tmem, unsigned long long da, unsigned
 // The S(S+1)/2 slice products of one K step, fully unrolled: product (i, j) accumulates into the
 // weight group w = min(i + j, 3); A slice i is read into the A collector once and reused by its
 // S - i products. FIRST: step 0 of a tile, where the first product of each group overwrites it.
-template <int S, bool FIRST>
+template <int S, int BN, bool FIRST>
 __device__ __forceinline__ void mma_kstep(unsigned tmem, unsigned long long da, unsigned long long db, unsigned idesc) {
 #pragma unroll
   for (int i = 0; i < S; ++i) {
 #pragma unroll
     for (int j = 0; i + j < S; ++j) {
-      constexpr int kA = (kSplitBM * 16 * 2) >> 4, kB = (128 * 16 * 2) >> 4;  // slice tile strides, 16-B units
+      constexpr int kA = (kSplitBM * 16 * 2) >> 4, kB = (BN * 16 * 2) >> 4;  // slice tile strides, 16-B units
       const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
-      const unsigned d_tmem = tmem + (unsigned)(w * 128);
+      const unsigned d_tmem = tmem + (unsigned)(w * BN);
       const unsigned long long a = da + (unsigned long long)(i * kA), b = db + (unsigned long long)(j * kB);
       const unsigned accum = (FIRST && i == 0 && j == w) ? 0u : 1u;
       const int uses = S - i;
@@ -463,18 +493,21 @@ __device__ inline bool epi_all(bool pred) {
   return r != 0;
 }
 
-template <int S>
+template <int S, int BN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_split_gemm_tc(SplitArgs a, int n_tiles) {
+  constexpr int kTcB = TcShape<BN>::kB, kAccCols = TcShape<BN>::kAccCols, kBufs = TcShape<BN>::kBufs;
+  constexpr int kQ = BN * 2 * S / kTcProducers;  // 16-byte B chunks per producer thread and K step
+  static_assert(kQ * kTcProducers == BN * 2 * S, "B chunks divide among the producers");
   extern __shared__ __align__(128) unsigned char smem_tc[];
   slice_t* As = reinterpret_cast<slice_t*>(smem_tc);  // [stages][S][kTcA]
   slice_t* Bs = As + kTcStages * S * kTcA;              // [stages][S][kTcB]
-  __shared__ __align__(8) unsigned long long full[kTcStages], fullA[kTcStages], empty[kTcStages], accbar, tmem_free,
-      donebar;
+  __shared__ __align__(8) unsigned long long full[kTcStages], fullA[kTcStages], empty[kTcStages], accbar[kBufs],
+      tmem_free[kBufs], donebar;
   __shared__ unsigned tmem_base_sh;
   __shared__ volatile int abort_sh;
-  __shared__ long long col_dst[kTcN];  // current tile, per column: destination offset, source exponent
-  __shared__ int col_e[kTcN];
+  __shared__ long long col_dst[BN];  // current tile, per column: destination offset, source exponent
+  __shared__ int col_e[BN];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == kTcMmaWarp) {
@@ -488,8 +521,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&fullA[s], 1);            // bulk copy of the A operand (byte count)
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&accbar, 1);
-    mbar_init(&tmem_free, kTcEpilogue);
+    for (int b = 0; b < kBufs; ++b) {
+      mbar_init(&accbar[b], 1);
+      mbar_init(&tmem_free[b], kTcEpilogue);
+    }
     mbar_init(&donebar, 1);
     abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n");
@@ -501,13 +536,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int nk = a.Kpad / kTcKC;
 
   if (warp < kTcProducers / 32) {
-    // ---- producers: a K step of the gathered operand is 128 columns x 2 S chunks of 16 bytes; a
+    // ---- producers: a K step of the gathered operand is BN columns x 2 S chunks of 16 bytes; a
     // column's chunks (slice, half) are contiguous in global memory, so consecutive threads take
-    // consecutive chunks: thread t copies chunks q = t + 256 i, i < S (column q / 2S, slice
+    // consecutive chunks: thread t copies chunks q = t + 256 i, i < kQ (column q / 2S, slice
     // (q % 2S) / 2, half q % 2)
-    const slice_t* bsrc[S];
-    int bdst[S];
-    bool bok[S];
+    const slice_t* bsrc[kQ];
+    int bdst[kQ];
+    bool bok[kQ];
     long long g = 0;  // ring step across tiles
     bool ok = true;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
@@ -515,7 +550,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // A: the S slices of K step k of this row tile are one contiguous block of S x 4 KB
       const slice_t* ablk = a.A + (a.a_mat[tile.group] * a.nrt + (tile.m0 >> 7)) * (long long)nk * S * kTcA;
 #pragma unroll
-      for (int i = 0; i < S; ++i) {
+      for (int i = 0; i < kQ; ++i) {
         const int q = tid + kTcProducers * i;
         const int col = q / (2 * S), w = q % (2 * S);
         const int sl = w >> 1, c = w & 1;
@@ -543,7 +578,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               : "memory");
         }
 #pragma unroll
-        for (int i = 0; i < S; ++i) cp_async16(Bs + st * S * kTcB + bdst[i], bsrc[i] + k * (S * 16), bok[i]);
+        for (int i = 0; i < kQ; ++i) cp_async16(Bs + st * S * kTcB + bdst[i], bsrc[i] + k * (S * 16), bok[i]);
         // arrives on full[st] once this thread's copies so far have landed; the thread moves on
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_u32(&full[st])) : "memory");
       }
@@ -563,8 +598,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int it = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
       const SplitTile tile = a.tiles[t];
-      if ((e & 1) == 0) {
-        const int col = e >> 1;
+      const int buf = it % kBufs;
+      if (e % (kTcEpilogue / BN) == 0) {
+        const int col = e / (kTcEpilogue / BN);
         const bool cok = col < tile.ncol;
         const long long v = cok ? a.src_vec[tile.col0 + col] : 0;
         col_dst[col] = cok ? a.dst_off[tile.col0 + col] : 0;
@@ -573,7 +609,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int row = tile.m0 + q * 32 + lane;
       const bool row_ok = row < a.M;
       const int era = row_ok ? a.ea[a.a_mat[tile.group] * a.ea_ld + row] : 0;
-      const bool acc_ok = mbar_wait(&accbar, (unsigned)it & 1u, &abort_sh);
+      const bool acc_ok = mbar_wait(&accbar[buf], (unsigned)(it / kBufs) & 1u, &abort_sh);
       // uniform over the epilogue group (also publishes the column metadata written above)
       if (!epi_all(acc_ok && !abort_sh)) {
         abort_sh = 1;
@@ -581,12 +617,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n");
 #pragma unroll 1
-      for (int cb = half * 4; cb < half * 4 + 4; ++cb) {
+      for (int cb = half * (BN / 32); cb < (half + 1) * (BN / 32); ++cb) {
         if (cb * 16 >= tile.ncol) break;
         float vv[kAcc][16];
 #pragma unroll
         for (int w = 0; w < kAcc; ++w) {
-          const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(w * kTcN + cb * 16);
+          const unsigned taddr =
+              tmem + ((unsigned)(q * 32) << 16) + (unsigned)(buf * kAccCols + w * BN + cb * 16);
           unsigned rr[16];
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
@@ -599,7 +636,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int cc = 0; cc < 16; ++cc) vv[w][cc] = __uint_as_float(rr[cc]);
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-        if (row_ok) {
+        if (row_ok && a.out_mode != 2) {
 #pragma unroll
           for (int cc = 0; cc < 16; ++cc) {
             const int col = cb * 16 + cc;
@@ -607,20 +644,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float h = vv[0][cc], l = 0.f;
 #pragma unroll
             for (int w = 1; w < kAcc; ++w) df_add(h, l, vv[w][cc]);
-            store_out(a, col_dst[col], row, h, l, era + col_e[col]);
+            store_out(a, col_dst[col], row, h, l, era + col_e[col], 0.0);
+          }
+        } else if (row_ok) {
+          // accumulating launch: fold first (the accumulators' registers are free again), then read
+          // the old values of eight columns together, then store them
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            float h = vv[0][cc], l = 0.f;
+#pragma unroll
+            for (int w = 1; w < kAcc; ++w) df_add(h, l, vv[w][cc]);
+            vv[0][cc] = h;
+            vv[1][cc] = l;
+          }
+#pragma unroll
+          for (int c8 = 0; c8 < 16; c8 += 8) {
+            double old[8];
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+              const int col = cb * 16 + c8 + cc;
+              old[cc] = col < tile.ncol ? reinterpret_cast<const double*>(a.Y)[col_dst[col] + row] : 0.0;
+            }
+#pragma unroll
+            for (int cc = 0; cc < 8; ++cc) {
+              const int col = cb * 16 + c8 + cc;
+              if (col < tile.ncol)
+                store_out(a, col_dst[col], row, vv[0][c8 + cc], vv[1][c8 + cc], era + col_e[col], old[cc]);
+            }
           }
         }
       }
       // accumulators read: the MMA warp may start the next tile
       asm volatile("tcgen05.fence::before_thread_sync;\n");
-      mbar_arrive(&tmem_free);
+      mbar_arrive(&tmem_free[buf]);
       // column metadata of this tile no longer needed by any epilogue thread
       asm volatile("bar.sync 1, %0;\n" ::"n"(kTcEpilogue) : "memory");
     }
   } else if (lane == 0) {
     // ---- MMA issuer
-    // instruction descriptor: D f32, A and B bf16, both K-major, N = 128, M = 128
-    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kTcN >> 3) << 17) |
+    // instruction descriptor: D f32, A and B bf16, both K-major, N = BN, M = 128
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) |
                            ((unsigned)(kSplitBM >> 4) << 24);
     // shared-memory descriptors of stage 0, slice 0; the start address (16-byte units, low bits) of
     // any other slice tile is an added constant, so a K step issues its S(S+1)/2 MMAs from
@@ -633,7 +696,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     bool ok = true;
     int it = 0;
     for (int t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++it) {
-      if (it > 0 && !mbar_wait(&tmem_free, (unsigned)(it - 1) & 1u, &abort_sh)) {
+      // the accumulator set of this tile is free once the epilogue has drained its previous use
+      const int buf = it % kBufs;
+      if (it >= kBufs && !mbar_wait(&tmem_free[buf], (unsigned)(it / kBufs - 1) & 1u, &abort_sh)) {
         ok = false;
         break;
       }
@@ -652,11 +717,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const unsigned long long da = dA0 + (unsigned long long)((st * S * kTcA * 2) >> 4);
         const unsigned long long db = dB0 + (unsigned long long)((st * S * kTcB * 2) >> 4);
         // the first product of each accumulator in a tile (step 0, i = 0, j = w) overwrites it
-        if (k == 0) mma_kstep<S, true>(tmem, da, db, idesc);
-        else mma_kstep<S, false>(tmem, da, db, idesc);
+        const unsigned acc = tmem + (unsigned)(buf * kAccCols);
+        if (k == 0) mma_kstep<S, BN, true>(acc, da, db, idesc);
+        else mma_kstep<S, BN, false>(acc, da, db, idesc);
         umma_commit(&empty[st]);
       }
-      if (ok) umma_commit(&accbar);
+      if (ok) umma_commit(&accbar[buf]);
     }
     if (!ok) abort_sh = 1;
     // every MMA issued above has completed once this arrives
@@ -674,7 +740,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-size_t tc_smem_bytes(int S) { return (size_t)kTcStages * S * (kTcA + kTcB) * sizeof(slice_t); }
+size_t tc_smem_bytes(int S, int BN) { return (size_t)kTcStages * S * (kTcA + BN * kTcKC) * sizeof(slice_t); }
 
 // ------------------------------------------------------------------ reduction
 
@@ -797,8 +863,10 @@ int prepare_split_launch() {
                            (int)mma_smem_bytes(kSplitSlices, 128, 64)));
   TRY(cudaFuncSetAttribute(k_split_gemm<kSplitSlices, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)mma_smem_bytes(kSplitSlices, 64, 32)));
-  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)tc_smem_bytes(kSplitSlices)));
+  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes(kSplitSlices, 128)));
+  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes(kSplitSlices, 64)));
   int sms = 0;
   TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   g_num_sms = sms > 0 ? sms : 1;
@@ -830,9 +898,12 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engin
     if (rc) return rc;
   }
   if (n_tiles <= 0) return VP_OK;
-  if (engine == kEngineTcgen05) {
+  if (engine == kEngineTcgen05 || engine == kEngineTcgen05N64) {
     const int grid = (short_ctas || n_tiles < g_num_sms) ? n_tiles : g_num_sms;
-    k_split_gemm_tc<kSplitSlices><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices), s>>>(a, n_tiles);
+    if (engine == kEngineTcgen05)
+      k_split_gemm_tc<kSplitSlices, 128><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 128), s>>>(a, n_tiles);
+    else
+      k_split_gemm_tc<kSplitSlices, 64><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 64), s>>>(a, n_tiles);
   }
   else if (engine == kEngineMmaSmall)
     k_split_gemm<kSplitSlices, 64, 32><<<n_tiles, 64, mma_smem_bytes(kSplitSlices, 64, 32), s>>>(a);

@@ -66,13 +66,16 @@ struct DFReduceArgs {
 };
 
 // GEMM engines for the sliced contraction: warp-level mma.sync on 128 x 64 tiles, tcgen05 with tensor
-// memory on 128 x 128 tiles, and mma.sync on 64 x 32 tiles (four times the CTAs of the first: for the
-// small, latency-bound launches of the coarse levels). vp_autotune chooses per launch shape.
-constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1, kEngineMmaSmall = 2;
-constexpr int kEngines = 3;
+// memory on 128 x 128 tiles, mma.sync on 64 x 32 tiles (four times the CTAs of the first: for the
+// small, latency-bound launches of the coarse levels), and tcgen05 on 128 x 64 tiles with two
+// accumulator sets in tensor memory (the epilogue of a tile overlaps the MMAs of the next: for
+// contractions with short K, whose tiles are bound by the epilogue). vp_autotune chooses per launch
+// shape.
+constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1, kEngineMmaSmall = 2, kEngineTcgen05N64 = 3;
+constexpr int kEngines = 4;
 constexpr int kSplitBM = 128;                             // rows of a table tile (the tiled layout's unit)
-constexpr int kSplitBMe[kEngines] = {128, 128, 64};       // rows per GEMM tile, by engine
-constexpr int kSplitBN[kEngines] = {64, 128, 32};         // columns per GEMM tile, by engine
+constexpr int kSplitBMe[kEngines] = {128, 128, 64, 128};  // rows per GEMM tile, by engine
+constexpr int kSplitBN[kEngines] = {64, 128, 32, 64};     // columns per GEMM tile, by engine
 
 int build_split(vp_tables_s* T, cudaStream_t s);
 void free_split_tables(vp_tables_s* T);

@@ -25,7 +25,7 @@ def _cuda():
 
 def _split_engines(w):
     """Split-precision results with the engines as bench.py chooses them (vp_autotune, then vp_eval
-    with the near field overlapping the far field), and with every launch on tcgen05."""
+    with the near field overlapping the far field), and with every launch on either tcgen05 engine."""
     import torch
     vp = V.VolumePotential(w.kernel, w.alpha, w.p, w.tree, precision=V.VP_PREC_SPLIT)
     try:
@@ -41,6 +41,11 @@ def _split_engines(w):
         torch.cuda.synchronize()
         V.vp_device_status()
         out["tcgen05"] = (u2.cpu().numpy(), g2[0].cpu().numpy(), g2[1].cpu().numpy())
+        V.vp_tree_set_engine(vp.tree, V.ENGINE_TCGEN05_N64)
+        u3, g3 = vp(f)
+        torch.cuda.synchronize()
+        V.vp_device_status()
+        out["tcgen05_n64"] = (u3.cpu().numpy(), g3[0].cpu().numpy(), g3[1].cpu().numpy())
         return out
     finally:
         vp.close()
