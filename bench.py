@@ -456,6 +456,26 @@ def layer_and_periodic(args, V):
                      "achieved": flops / (med / 1e3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": flops / (med / 1e3) / 1e12 / fp64_peak,
                      "flops_note": "10 n^2 log2 n per complex 2-D transform, 4 transforms"}}
+    # SISDC time stepping on the periodic box: Taylor-Green vortex, exact decay exp(-2 t / Re)
+    n, re, dt = 2048, 1.0, 0.01
+    u0, g0, l0 = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in I.taylor_green(n))
+    sdc = {}
+    for order in (2, 4):
+        st = V.SISDC(re, dt, order, n, 2 * np.pi)
+        try:
+            st.set(u0, g0, l0)
+            ms = timed_steps(lambda: st.step(1), steps, warmup, flush, stream)
+            u, _ = st.get()
+            T = (steps + warmup) * dt
+            err = float((u - u0 * np.exp(-2 * T / re)).abs().max() / u0.abs().max())
+        finally:
+            st.close()
+        med = statistics.median(ms)
+        solves = 1 if order == 1 else order * order - order
+        sdc[f"order_{order}"] = {"ms_per_step": med, "solves_per_step": solves, "ms_per_solve": med / solves,
+                                 "steps_per_s": 1e3 / med, "t_end": T, "rel_err_vs_exact": err}
+    out["sisdc"] = {"workload": f"Navier-Stokes on the periodic box [0, 2 pi)^2, {n}^2 grid, Re {re:g}, "
+                                f"Delta t {dt:g}, Taylor-Green vortex", **sdc}
     return out
 
 

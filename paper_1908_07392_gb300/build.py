@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libvp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["tables.cu", "eval.cu", "split.cu", "bie.cu", "ws.cu", "layer.cu", "periodic.cu"]
+CU_SOURCES = ["tables.cu", "eval.cu", "split.cu", "bie.cu", "ws.cu", "layer.cu", "periodic.cu", "sdc.cu"]
 CPP_SOURCES = ["plan.cpp"]
 HEADERS = ["special.cuh", "stokes.cuh", "layer.h", "vp_internal.h", "plan.h", "split.h", os.path.join("..", "..", "include", "vp.h"),
            os.path.join("..", "..", "include", "bie.h")]

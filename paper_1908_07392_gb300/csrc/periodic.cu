@@ -106,7 +106,10 @@ __global__ void k_spectral(int n, double alpha, double two_pi_over_L, const doub
     uy = make_double2(fy.x / (alpha * alpha), fy.y / (alpha * alpha));
   } else {
     const double den = 1.0 / (k2 * (alpha * alpha + k2));
-    const double sxx = ky * ky * den, sxy = -kx * ky * den, syy = kx * kx * den;
+    // on the Nyquist row or column (not the corner) the wavenumber n/2 stands for +n/2 and -n/2 alike,
+    // and the cross term, odd in it, averages to zero: the multiplier of a real field stays even
+    const bool nyq_edge = (ix == n / 2) != (iy == n / 2);
+    const double sxx = ky * ky * den, sxy = nyq_edge ? 0.0 : -kx * ky * den, syy = kx * kx * den;
     ux = make_double2(sxx * fx.x + sxy * fy.x, sxx * fx.y + sxy * fy.y);
     uy = make_double2(sxy * fx.x + syy * fy.x, sxy * fx.y + syy * fy.y);
   }

@@ -396,3 +396,42 @@ def step_workload(seed=5, depth=7, p=16, re=100.0, dt=1e-3, n_gauss=3, blend=0.0
 
     return StepWorkload(f"star_steps_uniform_d{depth}_p{p}_re{re:g}_dt{dt:g}", math.sqrt(re / dt), dt, p,
                         uniform_tree(depth, side=side), phi, source, moving_stokeslets(seed))
+
+
+# --------------------------------------------------------------------------- periodic flows
+
+def periodic_grid(n: int, side: float = 2 * np.pi):
+    """Uniform n x n grid of the periodic box [0, side)^2: X[j][i] = x_i, Y[j][i] = y_j."""
+    x = np.arange(n) * side / n
+    return np.meshgrid(x, x, indexing="xy")
+
+
+def taylor_green(n: int):
+    """The Taylor-Green vortex on [0, 2 pi)^2 at t = 0: u = (sin x cos y, -cos x sin y), its gradient
+    [a][m] = d u_a / d x_m and Laplacian -2 u, each [component][row j][column i]. It solves the
+    Navier-Stokes equations with u(t) = u(0) exp(-2 t / Re)."""
+    X, Y = periodic_grid(n)
+    u = np.stack([np.sin(X) * np.cos(Y), -np.cos(X) * np.sin(Y)])
+    g = np.stack([np.stack([np.cos(X) * np.cos(Y), -np.sin(X) * np.sin(Y)]),
+                  np.stack([np.sin(X) * np.sin(Y), -np.cos(X) * np.cos(Y)])])
+    return u, g, -2.0 * u
+
+
+INTERACTING_MODES = ((1, 2, 0.7, 0.3), (2, 1, -0.5, 1.1), (3, 1, 0.4, 2.0), (1, 3, 0.3, -0.7))
+
+
+def interacting_modes(n: int, modes=INTERACTING_MODES):
+    """A divergence-free field on [0, 2 pi)^2, u = (d psi / dy, -d psi / dx) for the stream function
+    psi = sum a cos(kx x + ky y + phase) over modes (kx, ky, a, phase), with its gradient and Laplacian
+    in closed form. The modes interact: (u . grad) u is not a gradient."""
+    X, Y = periodic_grid(n)
+    u = np.zeros((2, n, n)); g = np.zeros((2, 2, n, n)); lap = np.zeros((2, n, n))
+    for kx, ky, a, ph in modes:
+        th = kx * X + ky * Y + ph
+        s, c = np.sin(th), np.cos(th)
+        u[0] += -a * ky * s; u[1] += a * kx * s
+        g[0, 0] += -a * ky * kx * c; g[0, 1] += -a * ky * ky * c
+        g[1, 0] += a * kx * kx * c; g[1, 1] += a * kx * ky * c
+        k2 = kx * kx + ky * ky
+        lap[0] += a * ky * s * k2; lap[1] += -a * kx * s * k2
+    return u, g, lap

@@ -59,6 +59,25 @@ def test_against_oracle_every_point(n, alpha):
             assert np.abs(g[a, m] - go[a, m]).max() <= TOL * np.abs(go[a, m]).max()
 
 
+@pytest.mark.parametrize("n", [32, 64])
+def test_white_noise_with_nyquist_content(n):
+    # every mode present, the Nyquist row, column and corner included: the multiplier of a real field
+    # must stay even there (the oracle transforms each component separately and keeps the real part)
+    import torch
+    L, alpha = 2 * np.pi, 5.0
+    F = np.random.default_rng(n + 7).standard_normal((2, n, n))
+    P = V.PeriodicStokes(alpha, n, L)
+    try:
+        u, g = P(torch.from_numpy(F).cuda())
+        torch.cuda.synchronize()
+        u, g = u.cpu().numpy(), g.cpu().numpy()
+    finally:
+        P.close()
+    uo, go = PO.periodic_stokes(alpha, L, F)
+    assert np.abs(u - uo).max() <= TOL * np.abs(uo).max()
+    assert np.abs(g - go).max() <= TOL * np.abs(go).max()
+
+
 def test_against_the_tree_for_a_compact_divergence_free_force():
     # F = perp grad phi, phi a Gaussian well inside the box: u = (alpha^2 - Lap)^-1 F = G1 * F
     import torch

@@ -7,40 +7,17 @@ import numpy as np
 import pytest
 
 from oracle import sdc_oracle as SO
+from paper_1908_07392_gb300 import inputs as I
 
 L = 2 * np.pi
 
 
-def grid(n):
-    x = np.arange(n) * L / n
-    return np.meshgrid(x, x, indexing="xy")      # X[j][i] = x_i, Y[j][i] = y_j
-
-
 def taylor_green(n):
-    X, Y = grid(n)
-    u = np.stack([np.sin(X) * np.cos(Y), -np.cos(X) * np.sin(Y)])
-    g = np.stack([np.stack([np.cos(X) * np.cos(Y), -np.sin(X) * np.sin(Y)]),
-                  np.stack([np.sin(X) * np.sin(Y), -np.cos(X) * np.cos(Y)])])
-    return u, g, -2.0 * u
-
-
-MODES = [(1, 2, 0.7, 0.3), (2, 1, -0.5, 1.1), (3, 1, 0.4, 2.0), (1, 3, 0.3, -0.7)]
+    return I.taylor_green(n)
 
 
 def interacting_modes(n):
-    """u = (d psi / dy, -d psi / dx) for psi = sum a cos(kx x + ky y + phase), with its gradient and
-    Laplacian in closed form; the modes interact, so (u . grad) u is not a gradient."""
-    X, Y = grid(n)
-    u = np.zeros((2, n, n)); g = np.zeros((2, 2, n, n)); lap = np.zeros((2, n, n))
-    for kx, ky, a, ph in MODES:
-        th = kx * X + ky * Y + ph
-        s, c = np.sin(th), np.cos(th)
-        u[0] += -a * ky * s; u[1] += a * kx * s
-        g[0, 0] += -a * ky * kx * c; g[0, 1] += -a * ky * ky * c
-        g[1, 0] += a * kx * kx * c; g[1, 1] += a * kx * ky * c
-        k2 = kx * kx + ky * ky
-        lap[0] += a * ky * s * k2; lap[1] += -a * kx * s * k2
-    return u, g, lap
+    return I.interacting_modes(n)
 
 
 def test_quadrature_weights():
