@@ -142,6 +142,23 @@ __device__ inline void df_add(float& hi, float& lo, float x) {
   hi = t;
 }
 
+// s + e = a + b exactly (Knuth's TwoSum, no ordering of |a|, |b| assumed).
+__device__ inline void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// The four weight-group sums of one output as a double-float (h, l): groups 0 and 1 are exact
+// (K <= 256), so their sum is split exactly by TwoSum; the rounding error of that sum and groups 2
+// and 3 (below 2^-16 and 2^-24 of the result's scale) are added in fp32, whose rounding (2^-24 of
+// them) stays below the error group 2 already carries; a last TwoSum renormalises.
+__device__ inline void fold4(float a0, float a1, float a2, float a3, float& h, float& l) {
+  float s, e;
+  two_sum(a0, a1, s, e);
+  two_sum(s, __fadd_rn(__fadd_rn(e, a2), a3), h, l);
+}
+
 // 2^e as a float / double (e in the normal range of the type).
 __device__ inline float pow2f(int e) { return __int_as_float((e + 127) << 23); }
 __device__ inline double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
@@ -325,9 +342,9 @@ __global__ void __launch_bounds__(BM * BN / 32) k_split_gemm(SplitArgs a) {
         for (int rr = 0; rr < 2; ++rr) {
           const int row = tile.m0 + wm * 32 + mt * 16 + gid + rr * 8;
           if (row >= a.M) continue;
-          float h = 0.f, l = 0.f;
-#pragma unroll
-          for (int w = 0; w < kAcc; ++w) df_add(h, l, acc[w][mt][nt][rr * 2 + cc]);
+          float h, l;
+          fold4(acc[0][mt][nt][rr * 2 + cc], acc[1][mt][nt][rr * 2 + cc], acc[2][mt][nt][rr * 2 + cc],
+                acc[3][mt][nt][rr * 2 + cc], h, l);
           store_out(a, dst[cc], row, h, l, ea[row] + eb[cc], old[cc][mt][rr]);
         }
     }
@@ -339,7 +356,7 @@ size_t mma_smem_bytes(int S, int BM, int BN) { return (size_t)2 * S * (BM + BN) 
 // ------------------------------------------------------------------ engine 1: tcgen05
 //
 // Persistent and warp-specialised: one CTA per SM walks the tile list (tile t, t + gridDim.x, ...).
-//  * warps 0-7 (producers) stage the operands of every K step of 16 into a 4-stage ring in the
+//  * warps 0-3 (producers) stage the operands of every K step of 16 into a 4-stage ring in the
 //    canonical K-major layout without swizzle (8-row x 16-byte core matrices): the operator slices
 //    (A), stored in that layout tile by tile, by one bulk copy (cp.async.bulk, 24 KB) issued by
 //    thread 0, whose bytes complete on the stage's `fullA` mbarrier (next core matrix along K 2048
@@ -350,29 +367,35 @@ size_t mma_smem_bytes(int S, int BM, int BN) { return (size_t)2 * S * (BM + BN) 
 //    tiles, so the next tile's operands stream in while the current one is drained. (Moving A by a
 //    tensor map whose boxes are 16 bytes wide -- the same layout built by the TMA unit -- made the
 //    whole K step 1.7x slower: narrow boxes cost the unit far more than one contiguous copy.)
-//  * warp 16 (one thread) waits on `full`, fences the generic-proxy writes of the stage against
-//    the async proxy, issues tcgen05.mma (kind::f16, bf16 operands, M = 128,
-//    N = 128, K = 16) into four fp32 accumulators in tensor memory (one per weight group) and
-//    commits to the stage's `empty` mbarrier; after a tile's last step it commits to `acc`, and it
-//    starts the next tile once the epilogue has arrived on `tmem_free`.
-//  * warps 8-15 (epilogue) read the accumulators (warp w: tensor-memory lanes 32 (w % 4) .. + 31,
-//    one accumulator row per thread, half of the columns), fold them in double-float and store.
+//  * warps 4 .. 15 (epilogue) read the accumulators (warp w: tensor-memory lanes 32 (w % 4) .. + 31,
+//    one accumulator row per thread, every third block of 16 columns), fold them in double-float and
+//    store. (Three warps per lane quadrant: the epilogue is the part of a tile that the MMAs wait
+//    for, and four producer warps issue a K step's copies easily.)
+//  * warp 16 (one thread) waits on `full`, fences the generic-proxy writes of the stage against the
+//    async proxy, issues tcgen05.mma (kind::f16, bf16 operands, M = 128, N = BN, K = 16) into four
+//    fp32 accumulators in tensor memory (one per weight group) and commits to the stage's `empty`
+//    mbarrier; after a tile's last step it commits to `acc`, and it starts the next tile once the
+//    epilogue has arrived on `tmem_free`.
 // Every wait is bounded and also ends once another thread has given up; decisions taken by the
 // epilogue group are made uniform with a barrier reduction. A kernel that gave up raises a flag,
 // lets its issued MMAs finish (bounded), skips its remaining stores and releases tensor memory.
 
 __device__ int g_split_error = 0;
 
-constexpr int kTcProducers = 256;                 // warps 0-7
-constexpr int kTcEpilogue = 256;                  // warps 8-15
-constexpr int kTcMmaWarp = (kTcProducers + kTcEpilogue) / 32;  // warp 16
+constexpr int kTcProducers = 128;                 // warps 0-3
+#ifndef VP_TC_EPILOGUE_WARPS
+#define VP_TC_EPILOGUE_WARPS 12
+#endif
+constexpr int kTcEpilogue = 32 * VP_TC_EPILOGUE_WARPS;  // warps 8 .. 8 + warps - 1
+constexpr int kTcEpiParts = VP_TC_EPILOGUE_WARPS / 4;   // epilogue warps per tensor-memory lane quadrant
+constexpr int kTcMmaWarp = (kTcProducers + kTcEpilogue) / 32;
 constexpr int kTcThreads = kTcProducers + kTcEpilogue + 32;
 constexpr int kTcKC = 16;                         // K per stage
 constexpr int kTcStages = 4;
 constexpr int kTcCols = 512;                      // tensor-memory columns allocated per CTA
 constexpr int kTcA = kSplitBM * kTcKC;            // elements per A slice tile
 static_assert(kSplitBN[kEngineTcgen05] == 128 && kSplitBN[kEngineTcgen05N64] == 64, "tcgen05 tile widths");
-static_assert(kSplitBM == 128 && kTcProducers == 256 && kTcEpilogue == 256, "thread mapping");
+static_assert(kSplitBM == 128 && kTcProducers % 128 == 0 && kTcEpiParts * 128 == kTcEpilogue, "thread mapping");
 
 // Tile width BN (columns) of a tcgen05 engine: the four accumulators take 4 BN tensor-memory
 // columns, so at BN = 64 two sets fit and the MMAs of a tile run while the epilogue drains the
@@ -538,7 +561,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp < kTcProducers / 32) {
     // ---- producers: a K step of the gathered operand is BN columns x 2 S chunks of 16 bytes; a
     // column's chunks (slice, half) are contiguous in global memory, so consecutive threads take
-    // consecutive chunks: thread t copies chunks q = t + 256 i, i < kQ (column q / 2S, slice
+    // consecutive chunks: thread t copies chunks q = t + 128 i, i < kQ (column q / 2S, slice
     // (q % 2S) / 2, half q % 2)
     const slice_t* bsrc[kQ];
     int bdst[kQ];
@@ -594,7 +617,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   } else if (warp < kTcMmaWarp) {
     // ---- epilogue
     const int e = tid - kTcProducers;
-    const int q = warp & 3, half = (warp - kTcProducers / 32) >> 2;
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31; the kTcEpiParts warps of a quadrant share
+    // its column blocks
+    const int q = warp & 3, part = (warp - kTcProducers / 32) >> 2;
     int it = 0;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
       const SplitTile tile = a.tiles[t];
@@ -617,7 +642,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n");
 #pragma unroll 1
-      for (int cb = half * (BN / 32); cb < (half + 1) * (BN / 32); ++cb) {
+      for (int cb = part; cb < BN / 16; cb += kTcEpiParts) {
         if (cb * 16 >= tile.ncol) break;
         float vv[kAcc][16];
 #pragma unroll
@@ -641,9 +666,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int cc = 0; cc < 16; ++cc) {
             const int col = cb * 16 + cc;
             if (col >= tile.ncol) break;
-            float h = vv[0][cc], l = 0.f;
-#pragma unroll
-            for (int w = 1; w < kAcc; ++w) df_add(h, l, vv[w][cc]);
+            float h, l;
+            fold4(vv[0][cc], vv[1][cc], vv[2][cc], vv[3][cc], h, l);
             store_out(a, col_dst[col], row, h, l, era + col_e[col], 0.0);
           }
         } else if (row_ok) {
@@ -651,9 +675,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           // the old values of eight columns together, then store them
 #pragma unroll
           for (int cc = 0; cc < 16; ++cc) {
-            float h = vv[0][cc], l = 0.f;
-#pragma unroll
-            for (int w = 1; w < kAcc; ++w) df_add(h, l, vv[w][cc]);
+            float h, l;
+            fold4(vv[0][cc], vv[1][cc], vv[2][cc], vv[3][cc], h, l);
             vv[0][cc] = h;
             vv[1][cc] = l;
           }

@@ -86,3 +86,32 @@ def test_dropping_high_weights_costs_about_2_to_the_minus_48():
         ref = sum(Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b))
         bound = 2.0 ** -48 * (2.0 ** ea * np.abs(b).sum() + 2.0 ** eb * np.abs(a).sum()) + K * 2.0 ** (ea + eb - 56)
         assert abs(approx - ref) <= Fraction(bound)
+
+
+def _two_sum(a, b):
+    s = np.float32(a + b)
+    bb = np.float32(s - a)
+    e = np.float32(np.float32(a - np.float32(s - bb)) + np.float32(b - bb))
+    return s, e
+
+
+def test_fold_of_the_four_weight_groups():
+    # the device fold (split.cu fold4) in fp32: TwoSum of the exact groups 0 and 1, groups 2 and 3
+    # added to its error in fp32, a last TwoSum; h + l stays within 2^-23 (2^-24 |g0 + g1| + |g2| + |g3|)
+    # of the exact sum, whatever the signs and cancellation
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    for _ in range(5000):
+        g0 = np.float32(rng.integers(-2 ** 24, 2 ** 24))
+        g1 = np.float32(rng.integers(-2 ** 24, 2 ** 24) * 2.0 ** -8)
+        if rng.random() < 0.2:
+            g1 = np.float32(-g0 + rng.integers(-4, 4) * 2.0 ** -8)   # heavy cancellation
+        g2 = np.float32(rng.standard_normal() * 2.0 ** (8 - rng.integers(0, 12)))
+        g3 = np.float32(rng.standard_normal() * 2.0 ** (-rng.integers(0, 12)))
+        s, e = _two_sum(g0, g1)
+        h, l = _two_sum(s, np.float32(np.float32(e + g2) + g3))
+        exact = Fraction(float(g0)) + Fraction(float(g1)) + Fraction(float(g2)) + Fraction(float(g3))
+        err = abs(Fraction(float(h)) + Fraction(float(l)) - exact)
+        bound = Fraction(2) ** -23 * (Fraction(2) ** -24 * abs(Fraction(float(g0)) + Fraction(float(g1)))
+                                      + abs(Fraction(float(g2))) + abs(Fraction(float(g3))))
+        assert err <= bound, (g0, g1, g2, g3, float(err), float(bound))
