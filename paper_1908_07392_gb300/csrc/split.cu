@@ -661,7 +661,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int cc = 0; cc < 16; ++cc) vv[w][cc] = __uint_as_float(rr[cc]);
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;\n");
-        if (row_ok && a.out_mode != 2) {
+        if (row_ok && a.out_mode != 2 && cb * 16 + 16 <= tile.ncol) {
+          // a full block of 16 columns: no per-column exit, so the columns' independent chains
+          // (metadata load, fold, store) interleave
+#pragma unroll
+          for (int cc = 0; cc < 16; ++cc) {
+            const int col = cb * 16 + cc;
+            float h, l;
+            fold4(vv[0][cc], vv[1][cc], vv[2][cc], vv[3][cc], h, l);
+            store_out(a, col_dst[col], row, h, l, era + col_e[col], 0.0);
+          }
+        } else if (row_ok && a.out_mode != 2) {
 #pragma unroll
           for (int cc = 0; cc < 16; ++cc) {
             const int col = cb * 16 + cc;
