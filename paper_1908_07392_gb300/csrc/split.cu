@@ -149,14 +149,17 @@ __device__ inline void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// The four weight-group sums of one output as a double-float (h, l): groups 0 and 1 are exact
-// (K <= 256), so their sum is split exactly by TwoSum; the rounding error of that sum and groups 2
-// and 3 (below 2^-16 and 2^-24 of the result's scale) are added in fp32, whose rounding (2^-24 of
-// them) stays below the error group 2 already carries; a last TwoSum renormalises.
+// The four weight-group sums of one output as a double-float (h, l): groups 0, 1 and 2 enter through
+// TwoSums (exact), so only the two rounding errors those leave (each below 2^-24 of a partial sum)
+// and group 3 (the tail, below 2^-24 of the scale) are added in fp32; a last TwoSum renormalises.
+// h + l is within 2^-23 (|e| + |e2| + |a3|) <= about 2^-47 of the partial sums of the exact total.
+// (Group 2 added in fp32 as well costs 2^-24 of it, which cancellation in the contraction makes
+// visible: gradients of the star workload at 2e-9 instead of 1e-10.)
 __device__ inline void fold4(float a0, float a1, float a2, float a3, float& h, float& l) {
-  float s, e;
+  float s, e, s2, e2;
   two_sum(a0, a1, s, e);
-  two_sum(s, __fadd_rn(__fadd_rn(e, a2), a3), h, l);
+  two_sum(s, a2, s2, e2);
+  two_sum(s2, __fadd_rn(__fadd_rn(e, e2), a3), h, l);
 }
 
 // 2^e as a float / double (e in the normal range of the type).
