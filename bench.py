@@ -44,7 +44,23 @@ FP64_FLOPS_PER_CLK_PER_SM = 4.0   # 2 DFMA per clock per SM: 1.25 TFLOP/s nomina
 # by pairs to the 356k pairs at depth 10.
 TRAFFIC_FP64_NEAR = 3.68e9
 TRAFFIC_FP64_NEAR_SOURCE = "constant from a past ncu capture (profiles/near_f64_star_d8.md, depth 8 scaled by near pairs)"
+# DRAM bytes of the split-precision near-field launch (tcgen05 engine) per algorithmic GFLOP of the near
+# stage, NOT measured in this run: the ncu capture of the same kernel at depth 8 (419.3 MB read + 419.2
+# MB written for 29.33 GFLOP, profiles/near_tc_star_d8.md); traffic grows with the near pairs, i.e. with
+# the stage's flops.
+TRAFFIC_SPLIT_NEAR_PER_GFLOP = 838.5e6 / 29.33
+TRAFFIC_SPLIT_NEAR_SOURCE = ("constant from an ncu capture (profiles/near_tc_star_d8.md, depth 8, 838.5 MB for 29.33 "
+                             "GFLOP) scaled by the near stage's flops")
 N_SM = 152
+ENGINE_NAMES = {-1: "-", 0: "mma.sync 128x64", 1: "tcgen05 128x128", 2: "mma.sync 64x32", 3: "tcgen05 128x64"}
+
+
+def launch_list_engine(launch_list, table):
+    """Engine of the (first) split contraction on operator table `table` in a launch list, or -1."""
+    for x in launch_list:
+        if x["kind"] == 4 and x["table"] == table:
+            return x["engine"]
+    return -1
 SLICE_PRODUCTS = 21  # S (S + 1) / 2 slice products per contraction, S = 6 bf16 slices
 
 
@@ -686,6 +702,9 @@ def measure(args, V, w, prec, world, local, with_e2e):
                     "bound": "tensor", "peak_source": "measured dense bf16 burst (MEASURED_PEAKS.json), of measured",
                     "fp64_equivalent_tflops": near_flops / (near_ms / 1000.0) / 1e12}
             traffic = None
+            if args.engine in ("auto", "tcgen05") and launch_list_engine(launch_list, 0) == 1:
+                traffic = near_flops / 1e9 * TRAFFIC_SPLIT_NEAR_PER_GFLOP
+                roof["traffic_source"] = TRAFFIC_SPLIT_NEAR_SOURCE
         roof.update(algorithmic_bytes=stage_bytes[4], achieved_gbs=near_gbs, hbm_frac_of_measured=near_gbs / hbm)
 
         def rate(flops, bytes_, ms):
@@ -708,7 +727,7 @@ def measure(args, V, w, prec, world, local, with_e2e):
                              index=i, kind=kinds.get(launch_list[i]["kind"], "?"),
                              stage=V.STAGE_NAMES[launch_list[i]["stage"]],
                              table=tables.get(launch_list[i]["table"], "?"),
-                             engine={-1: "-", 0: "mma.sync", 1: "tcgen05"}.get(launch_list[i]["engine"], "?"))
+                             engine=ENGINE_NAMES.get(launch_list[i]["engine"], "?"))
                         for i in top]
         return {"value": value, "total_ms": total_ms, "N": N, "setup_s": setup_s, "n_tc": n_tc,
                 "u": u.cpu().numpy(), "g": g.cpu().numpy(),
