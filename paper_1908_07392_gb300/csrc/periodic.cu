@@ -23,7 +23,7 @@
 struct vp_periodic_s {
   double alpha = 0.0, side = 0.0;
   int n = 0, logn = 0;
-  double2* tw_f = nullptr;  // e^{-2 pi i q / n}, q < n/2
+  double2* tw_f = nullptr;  // e^{-2 pi i q / n}, q < n
   double2* tw_i = nullptr;  // e^{+2 pi i q / n}
   double2* a = nullptr;     // work arrays [n][n]
   double2* b = nullptr;
@@ -41,31 +41,52 @@ constexpr int kMaxN = 4096;
 
 __device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
-// One length-n transform per block (row blockIdx.x of data [rows][n]), in place, unnormalised.
-// Stage t (l = n / 2^t, m = 2^(t-1)): y[k + 2 j m] = x[k + j m] + x[k + j m + l m],
-// y[k + 2 j m + m] = w^j (x[k + j m] - x[k + j m + l m]),  w = e^(-+2 pi i / (2 l)).
-__global__ void __launch_bounds__(kFftThreads) k_fft_rows(int n, int logn, double2* data, const double2* tw) {
+// One length-n transform per block (row blockIdx.x of data [rows][n]), in place, unnormalised: Stockham
+// autosort, decimation in frequency, radix 4 (and one radix-2 stage when log2 n is odd), ping-pong in
+// shared memory. A stage of radix r with m points already combined (l = n / (r m)) maps, for j < l and
+// k < m, the inputs a_q = x[k + (j + q l) m] (q < r) to
+//   y[k + (r j + p) m] = w^(p j m) b_p,   b_p = sum_q a_q e^(-+2 pi i p q / r),   w = e^(-+2 pi i / n),
+// then m *= r. `dir` is the sign of the exponent (-1 forward, +1 inverse) and tw[q] = e^(dir 2 pi i q / n).
+__device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+__global__ void __launch_bounds__(kFftThreads) k_fft_rows(int n, int logn, int dir, double2* data, const double2* tw) {
   extern __shared__ double2 fsm[];
   double2* x = fsm;
   double2* y = fsm + n;
   double2* row = data + (size_t)blockIdx.x * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = row[i];
   __syncthreads();
-  const int half = n >> 1;
   int lg_m = 0;  // log2 m
-  for (int t = 0; t < logn; ++t) {
-    const int lg_l = logn - 1 - t;  // l = n / 2^(t+1)
-    const int m = 1 << lg_m, l = 1 << lg_l;
-    for (int idx = threadIdx.x; idx < half; idx += blockDim.x) {
-      const int j = idx >> lg_m, k = idx & (m - 1);
-      const double2 c0 = x[k + j * m], c1 = x[k + j * m + l * m];
-      const double2 w = tw[j << t];  // e^(-+2 pi i j / (2l)) = tw[j n / (2l)]
-      y[k + 2 * j * m] = make_double2(c0.x + c1.x, c0.y + c1.y);
-      y[k + 2 * j * m + m] = cmul(w, make_double2(c0.x - c1.x, c0.y - c1.y));
+  if (logn & 1) {
+    // radix-2 stage first (m = 1, l = n / 2): twiddle index p j m = j for p = 1
+    const int l = n >> 1;
+    for (int j = threadIdx.x; j < l; j += blockDim.x) {
+      const double2 a0 = x[j], a1 = x[j + l];
+      y[2 * j] = cadd(a0, a1);
+      y[2 * j + 1] = cmul(tw[j], csub(a0, a1));
     }
     __syncthreads();
-    double2* s = x; x = y; y = s;
-    ++lg_m;
+    double2* t = x; x = y; y = t;
+    lg_m = 1;
+  }
+  for (; lg_m < logn; lg_m += 2) {
+    const int m = 1 << lg_m, lg_l = logn - 2 - lg_m, l = 1 << lg_l;
+    for (int idx = threadIdx.x; idx < (n >> 2); idx += blockDim.x) {
+      const int j = idx >> lg_m, k = idx & (m - 1);
+      const int i0 = k + j * m, lm = l * m;
+      const double2 a0 = x[i0], a1 = x[i0 + lm], a2 = x[i0 + 2 * lm], a3 = x[i0 + 3 * lm];
+      const double2 s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+      // e^(dir i pi / 2) (a1 - a3) = dir i d13
+      const double2 r13 = make_double2(-dir * d13.y, dir * d13.x);
+      const int o = k + 4 * j * m, jm = j * m;
+      y[o] = cadd(s02, s13);
+      y[o + m] = cmul(tw[jm], cadd(d02, r13));
+      y[o + 2 * m] = cmul(tw[2 * jm], csub(s02, s13));
+      y[o + 3 * m] = cmul(tw[3 * jm], csub(d02, r13));
+    }
+    __syncthreads();
+    double2* t = x; x = y; y = t;
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) row[i] = x[i];
 }
@@ -133,7 +154,7 @@ __global__ void k_unpack(long long nn, const double2* z, double* re, double* im)
 
 __global__ void k_twiddles(int n, double sign, double2* tw) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n / 2) return;
+  if (q >= n) return;
   double s, c;
   sincospi(2.0 * q / n, &s, &c);
   tw[q] = make_double2(c, sign * s);
@@ -142,14 +163,14 @@ __global__ void k_twiddles(int n, double sign, double2* tw) {
 size_t fft_smem(int n) { return (size_t)2 * n * sizeof(double2); }
 
 // 2D transform of X [n][n] in place (rows, transpose into W, rows, transpose back).
-int fft2d(const vp_periodic_s* P, double2* X, double2* W, const double2* tw, cudaStream_t s) {
+int fft2d(const vp_periodic_s* P, double2* X, double2* W, const double2* tw, int dir, cudaStream_t s) {
   const int n = P->n;
-  k_fft_rows<<<n, kFftThreads, fft_smem(n), s>>>(n, P->logn, X, tw);
+  k_fft_rows<<<n, kFftThreads, fft_smem(n), s>>>(n, P->logn, dir, X, tw);
   TRY(cudaGetLastError());
   const dim3 tg(n / 32, n / 32), tb(32, 8);
   k_transpose<<<tg, tb, 0, s>>>(n, X, W);
   TRY(cudaGetLastError());
-  k_fft_rows<<<n, kFftThreads, fft_smem(n), s>>>(n, P->logn, W, tw);
+  k_fft_rows<<<n, kFftThreads, fft_smem(n), s>>>(n, P->logn, dir, W, tw);
   TRY(cudaGetLastError());
   k_transpose<<<tg, tb, 0, s>>>(n, W, X);
   TRY(cudaGetLastError());
@@ -175,13 +196,13 @@ extern "C" int vp_periodic_create(double alpha, int n, double side, void* stream
   for (double2** p : {&P->a, &P->b, &P->c, &P->d}) {
     if (cudaMalloc(p, nn * sizeof(double2)) != cudaSuccess) { cudaGetLastError(); return fail(VP_ERR_OOM); }
   }
-  if (cudaMalloc(&P->tw_f, (n / 2) * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(&P->tw_i, (n / 2) * sizeof(double2)) != cudaSuccess) {
+  if (cudaMalloc(&P->tw_f, n * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&P->tw_i, n * sizeof(double2)) != cudaSuccess) {
     cudaGetLastError();
     return fail(VP_ERR_OOM);
   }
-  k_twiddles<<<(n / 2 + 255) / 256, 256, 0, s>>>(n, -1.0, P->tw_f);
-  k_twiddles<<<(n / 2 + 255) / 256, 256, 0, s>>>(n, 1.0, P->tw_i);
+  k_twiddles<<<(n + 255) / 256, 256, 0, s>>>(n, -1.0, P->tw_f);
+  k_twiddles<<<(n + 255) / 256, 256, 0, s>>>(n, 1.0, P->tw_i);
   if (cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem(kMaxN)) !=
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
@@ -200,14 +221,14 @@ extern "C" int vp_periodic_eval(vp_periodic P, const double* F, double* u, doubl
   const unsigned g = (unsigned)((nn + 255) / 256);
   k_pack<<<g, 256, 0, s>>>(nn, F, F + nn, P->a);
   TRY(cudaGetLastError());
-  int rc = fft2d(P, P->a, P->b, P->tw_f, s);
+  int rc = fft2d(P, P->a, P->b, P->tw_f, -1, s);
   if (rc) return rc;
   // spectra of (u_x + i u_y), (d_x u_x + i d_y u_x), (d_x u_y + i d_y u_y)
   k_spectral<<<g, 256, 0, s>>>(n, P->alpha, 2.0 * kPi / P->side, P->a, P->b, P->c, P->d);
   TRY(cudaGetLastError());
   for (int f = 0; f < 3; ++f) {
     double2* X = f == 0 ? P->b : (f == 1 ? P->c : P->d);
-    if ((rc = fft2d(P, X, P->a, P->tw_i, s))) return rc;
+    if ((rc = fft2d(P, X, P->a, P->tw_i, 1, s))) return rc;
     double* re = f == 0 ? u : gradu + (size_t)(f - 1) * 2 * nn;
     double* im = f == 0 ? u + nn : re + nn;
     k_unpack<<<g, 256, 0, s>>>(nn, X, re, im);
