@@ -1055,7 +1055,7 @@ SplitArgs split_args(const vp_tree_s* tr, const DevSplit& d, double* const* bufs
 // Issue one evaluation. With per-stage events (ev) every step goes to `s` in order. Otherwise the
 // near-field steps, which need only the source (and its slices), run on `s` while the far-field
 // chain (upward, M2L, downward, targets) runs on the tree's high-priority side stream; near-field
-// CTAs then hold one tile each, so chain launches find SMs; `s` waits for the chain before the
+// CTAs then hold two tiles each, so chain launches find SMs; `s` waits for the chain before the
 // output reduction. The two write disjoint contribution slots.
 // With per-step events (step_ev, steps + 1 of them) every step goes to `s` in order and an event is
 // recorded before each step and after the last.

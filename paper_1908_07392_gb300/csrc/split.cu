@@ -935,7 +935,10 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engin
   }
   if (n_tiles <= 0) return VP_OK;
   if (engine == kEngineTcgen05 || engine == kEngineTcgen05N64) {
-    const int grid = (short_ctas || n_tiles < g_num_sms) ? n_tiles : g_num_sms;
+    // short_ctas: two tiles per CTA (CTAs end often enough for the far-field chain's launches to find
+    // SMs, and the per-CTA setup is paid half as often: 7.00 vs 7.17 ms per overlapped evaluation of
+    // the full-size star, 7.07 with four)
+    const int grid = short_ctas ? (n_tiles + 1) / 2 : (n_tiles < g_num_sms ? n_tiles : g_num_sms);
     if (engine == kEngineTcgen05)
       k_split_gemm_tc<kSplitSlices, 128><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 128), s>>>(a, n_tiles);
     else

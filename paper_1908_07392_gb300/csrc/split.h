@@ -80,7 +80,7 @@ constexpr int kSplitBN[kEngines] = {64, 128, 32, 64};     // columns per GEMM ti
 int build_split(vp_tables_s* T, cudaStream_t s);
 void free_split_tables(vp_tables_s* T);
 int prepare_split_launch();
-// short_ctas: tcgen05 CTAs take one tile each (so other kernels can interleave) instead of one
+// short_ctas: tcgen05 CTAs take two tiles each (so other kernels can interleave) instead of one
 // persistent CTA per SM.
 int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engine, int short_ctas = 0);
 // Read and clear the flag that a bounded wait of the tcgen05 engine gave up.
