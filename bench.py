@@ -17,12 +17,13 @@ vp_eval_host from pinned host buffers (host-to-device copy of f and
 device-to-host copy of u and grad u inside the timed region). The CPU baseline
 is the FP64 oracle on a bounded sample of targets of the same workload.
 
-Other workloads: --workload batched (64 trees in one CUDA graph) and
+Other workloads: --workload batched (64 trees in one CUDA graph),
 --workload steps (coupled volume potential + boundary integral equation steps
-with the learned GMRES warm start).
+with the learned GMRES warm start) and --workload periodic (the periodic FFT
+solution and SISDC steps alone).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                       [--precision both|fp64|split] [--workload star|batched|steps]
+                       [--precision both|fp64|split] [--workload star|batched|steps|periodic]
 """
 from __future__ import annotations
 
@@ -80,7 +81,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched workload that the default run measures beside the headline")
     ap.add_argument("--max-depth", type=int, default=10, help="tree depth cap (10 = the stated workload)")
-    ap.add_argument("--workload", default="star", choices=["star", "batched", "steps"],
+    ap.add_argument("--workload", default="star", choices=["star", "batched", "steps", "periodic"],
                     help="star: one adaptive tree (default); batched: 64 trees in one CUDA graph; "
                          "steps: coupled volume potential + boundary solve with the learned warm start")
     ap.add_argument("--train-steps", type=int, default=2000, help="steps workload: plain solves to train on")
@@ -442,6 +443,17 @@ def layer_and_periodic(args, V):
         if vp is not None:
             vp.close()
         b.close()
+    out.update(periodic_and_sdc(args, V, steps, warmup, flush, stream))
+    return out
+
+
+def periodic_and_sdc(args, V, steps, warmup, flush, stream):
+    """The periodic FFT solution (u and grad u) on a 4096^2 grid against a manufactured exact solution,
+    and SISDC steps of orders 2 and 4 on a 2048^2 Taylor-Green vortex against its exact decay."""
+    import numpy as np
+    import torch
+    from paper_1908_07392_gb300 import inputs as I
+    out = {}
     # periodic FFT solution: manufactured divergence-free velocity with a pressure gradient added
     n, L, alpha = 4096, 3.0, 316.0
     x = torch.arange(n, dtype=torch.float64, device="cuda") * (L / n)
@@ -462,13 +474,13 @@ def layer_and_periodic(args, V):
     finally:
         P.close()
     med = statistics.median(ms)
-    flops = 4 * 10.0 * n * n * np.log2(n)  # one forward and three inverse complex 2-D transforms, radix 2
+    flops = 4 * 10.0 * n * n * np.log2(n)  # one forward and three inverse complex 2-D transforms (nominal count)
     fp64_peak = N_SM * 2070.0e6 * FP64_FLOPS_PER_CLK_PER_SM / 1e12
     out["periodic_fft"] = {
         "workload": f"periodic modified Stokes velocity and gradient on a {n}^2 grid, box side 3, alpha 316",
         "value": n * n / (med / 1e3), "unit": "grid points/s", "ms_per_eval": med, "steps": steps,
         "rel_err_vs_manufactured": err,
-        "roofline": {"bound": "alu", "kernel": "FP64 radix-2 butterflies (shared memory)",
+        "roofline": {"bound": "alu", "kernel": "k_fft_rows: FP64 radix-4 Stockham rows in shared memory",
                      "achieved": flops / (med / 1e3) / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                      "frac": flops / (med / 1e3) / 1e12 / fp64_peak,
                      "flops_note": "10 n^2 log2 n per complex 2-D transform, 4 transforms"}}
@@ -493,6 +505,26 @@ def layer_and_periodic(args, V):
     out["sisdc"] = {"workload": f"Navier-Stokes on the periodic box [0, 2 pi)^2, {n}^2 grid, Re {re:g}, "
                                 f"Delta t {dt:g}, Taylor-Green vortex", **sdc}
     return out
+
+
+def run_periodic(args):
+    """The periodic FFT solution and SISDC steps alone (the parts of the default line that need no
+    tree), as one JSON line: a small command for profiling these kernels."""
+    import torch
+    import paper_1908_07392_gb300 as V
+    from paper_1908_07392_gb300 import build as B
+    B.build()
+    steps, warmup = max(1, min(args.steps, 10)), max(1, args.warmup)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with ClockSampler(torch.cuda.current_device()) as sampler:
+        res = periodic_and_sdc(args, V, steps, warmup, flush, torch.cuda.current_stream())
+    p = res["periodic_fft"]
+    line = {"metric": "periodic modified Stokes solution grid points/s", "value": p["value"], "unit": p["unit"],
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": p["ms_per_eval"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": p["workload"]}, "roofline": p["roofline"], "sisdc": res["sisdc"],
+            "rel_err_vs_manufactured": p["rel_err_vs_manufactured"], "clocks": sampler.summary()}
+    print(json.dumps(line), flush=True)
 
 
 def run_batched(args):
@@ -753,6 +785,9 @@ def main():
         return
     if args.workload == "steps":
         run_steps(args)
+        return
+    if args.workload == "periodic":
+        run_periodic(args)
         return
     import torch
     import paper_1908_07392_gb300 as V
