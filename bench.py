@@ -53,7 +53,8 @@ TRAFFIC_SPLIT_NEAR_PER_GFLOP = 838.5e6 / 29.33
 TRAFFIC_SPLIT_NEAR_SOURCE = ("constant from an ncu capture (profiles/near_tc_star_d8.md, depth 8, 838.5 MB for 29.33 "
                              "GFLOP) scaled by the near stage's flops")
 N_SM = 152
-ENGINE_NAMES = {-1: "-", 0: "mma.sync 128x64", 1: "tcgen05 128x128", 2: "mma.sync 64x32", 3: "tcgen05 128x64"}
+ENGINE_NAMES = {-1: "-", 0: "mma.sync 128x64", 1: "tcgen05 128x128", 2: "mma.sync 64x32", 3: "tcgen05 128x64",
+                4: "tcgen05 transposed 128x128"}
 
 
 def launch_list_engine(launch_list, table):

@@ -382,12 +382,15 @@ int vp_eval_static(vp_tree tree, const double* f, double* u, double* gradu, void
  *     time is the latency of a few tiles);
  *  3  tcgen05 as engine 1 on tiles of 128 x 64, with two sets of four accumulators in tensor
  *     memory, so that the epilogue of one tile overlaps the MMAs of the next (for short K, where
- *     draining the accumulators takes longer than filling them).
+ *     draining the accumulators takes longer than filling them);
+ *  4  tcgen05 on transposed tiles: the tile's 128 columns are the MMA's rows and the operator's rows
+ *     its N (rounded up to 96 or 128), so operators of at most 128 rows (the 81-row multipole and
+ *     local operators) fill every tensor-memory lane; launches with taller operators run on engine 1.
  * All compute the same exact slice sums. vp_tree_set_engine sets one engine for every launch of
  * the tree (VP_ERR_ARG for other values). vp_autotune times each split-precision launch of one
  * evaluation of `f` with every engine (tile shape) on `stream`, keeps the fastest per launch shape,
  * evaluates once more into u, gradu with the choice, and, if *n_tcgen05 is given, reports how many
- * launches use a tcgen05 engine (1 or 3).
+ * launches use a tcgen05 engine (1, 3 or 4).
  * With cache_path (may be NULL) the choices are read from / appended to a text file keyed by
  * (p, P, channels, operator, rows, padded K, tiles). Trees on FP64 tables are left unchanged.
  * vp_device_status reads and clears the device flag a bounded wait sets when it gives up:

@@ -143,6 +143,7 @@ ENGINE_MMA_SYNC = 0
 ENGINE_TCGEN05 = 1
 ENGINE_MMA_SMALL = 2
 ENGINE_TCGEN05_N64 = 3
+ENGINE_TCGEN05_T = 4
 
 
 def vp_tree_set_engine(tree: int, engine: int):

@@ -1530,7 +1530,7 @@ extern "C" int vp_autotune(vp_tree tree, const double* f, double* u, double* gra
   int ntc = 0;
   for (int k = 0; k < ns; ++k) {
     tree->splits[k].engine = choice[k];
-    ntc += choice[k] == kEngineTcgen05 || choice[k] == kEngineTcgen05N64;
+    ntc += choice[k] == kEngineTcgen05 || choice[k] == kEngineTcgen05N64 || choice[k] == kEngineTcgen05T;
   }
   if (n_tcgen05) *n_tcgen05 = ntc;
   // leave u, gradu holding a valid evaluation with the chosen engines

@@ -171,6 +171,24 @@ __device__ inline double pow2d(int e) { return __longlong_as_double((long long)(
 // Scaling by a power of two is exact (ldexp only where 2^e itself is not a normal number). Callers
 // with out_mode 2 read the old values of a group of outputs first, so that the reads of the group
 // are in flight together instead of one read-add-store chain per element.
+// The 8 bytes store_out would write for out_mode 0 (double-float slot) or 1 (FP64), as a double.
+__device__ inline double out_value(const SplitArgs& a, float h, float l, int e) {
+  if (a.out_mode == 0) {
+    float2 o;
+    if (e >= -126 && e <= 127) {
+      const float sc = pow2f(e);
+      o.x = h * sc;
+      o.y = l * sc;
+    } else {
+      o.x = ldexpf(h, e);
+      o.y = ldexpf(l, e);
+    }
+    return __hiloint2double(__float_as_int(o.y), __float_as_int(o.x));
+  }
+  const double hl = (double)h + (double)l;
+  return (e >= -1022 && e <= 1023) ? hl * pow2d(e) : ldexp(hl, e);
+}
+
 __device__ inline void store_out(const SplitArgs& a, long long dst, int row, float h, float l, int e, double old) {
   if (a.out_mode == 0) {
     float2 o;
@@ -454,15 +472,17 @@ __device__ inline void umma_f16(unsigned d_tmem, unsigned long long da, unsigned
 // The S(S+1)/2 slice products of one K step, fully unrolled: product (i, j) accumulates into the
 // weight group w = min(i + j, 3); A slice i is read into the A collector once and reused by its
 // S - i products. FIRST: step 0 of a tile, where the first product of each group overwrites it.
-template <int S, int BN, bool FIRST>
+// W: columns of one accumulator; KA, KB: strides between the slice tiles of the A and B operands in
+// shared memory (16-byte units).
+template <int S, int W, int KA, int KB, bool FIRST>
 __device__ __forceinline__ void mma_kstep(unsigned tmem, unsigned long long da, unsigned long long db, unsigned idesc) {
 #pragma unroll
   for (int i = 0; i < S; ++i) {
 #pragma unroll
     for (int j = 0; i + j < S; ++j) {
-      constexpr int kA = (kSplitBM * 16 * 2) >> 4, kB = (BN * 16 * 2) >> 4;  // slice tile strides, 16-B units
+      constexpr int kA = KA, kB = KB;
       const int w = (i + j < kAcc - 1) ? i + j : kAcc - 1;
-      const unsigned d_tmem = tmem + (unsigned)(w * BN);
+      const unsigned d_tmem = tmem + (unsigned)(w * W);
       const unsigned long long a = da + (unsigned long long)(i * kA), b = db + (unsigned long long)(j * kB);
       const unsigned accum = (FIRST && i == 0 && j == w) ? 0u : 1u;
       const int uses = S - i;
@@ -519,10 +539,18 @@ __device__ inline bool epi_all(bool pred) {
   return r != 0;
 }
 
-template <int S, int BN>
+// TR = 0: D [operator rows x columns] = operator slices (A) x gathered vectors (B), N = BN.
+// TR > 0 (operators of at most TR <= 128 rows, BN = 128): the transposed product D^T [columns x rows]
+// = gathered vectors (A, M = 128) x operator slices (B, N = TR), so every tensor-memory lane -- and
+// every epilogue thread -- holds one of the tile's 128 columns even when the operator has only 81
+// rows (the multipole and local operators). The shared-memory layouts are the same; only the
+// descriptors trade places.
+template <int S, int BN, int TR>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_split_gemm_tc(SplitArgs a, int n_tiles) {
-  constexpr int kTcB = TcShape<BN>::kB, kAccCols = TcShape<BN>::kAccCols, kBufs = TcShape<BN>::kBufs;
+  static_assert(TR == 0 || (BN == 128 && TR % 16 == 0 && TR <= 128), "transposed tiles");
+  constexpr int kTcB = TcShape<BN>::kB;
+  constexpr int kAccCols = TR ? kAcc * TR : TcShape<BN>::kAccCols, kBufs = TR ? 1 : TcShape<BN>::kBufs;
   constexpr int kQ = BN * 2 * S / kTcProducers;  // 16-byte B chunks per producer thread and K step
   static_assert(kQ * kTcProducers == BN * 2 * S, "B chunks divide among the producers");
   extern __shared__ __align__(128) unsigned char smem_tc[];
@@ -534,6 +562,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ volatile int abort_sh;
   __shared__ long long col_dst[BN];  // current tile, per column: destination offset, source exponent
   __shared__ int col_e[BN];
+  // transposed tiles: per epilogue warp, eight outputs of its 32 lanes' destinations on their way to
+  // coalesced stores
+  __shared__ __align__(16) double stage[TR ? kTcEpilogue / 32 : 1][32][8];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == kTcMmaWarp) {
@@ -619,6 +650,109 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
   } else if (warp < kTcMmaWarp) {
     // ---- epilogue
+    if constexpr (TR > 0) {
+      // transposed tiles: lane = column of the tile (vector, destination), tensor-memory column =
+      // operator row
+      const int e = tid - kTcProducers;
+      const int q = warp & 3, part = (warp - kTcProducers / 32) >> 2;
+      int it = 0;
+      for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++it) {
+        const SplitTile tile = a.tiles[t];
+        for (int o = e; o < TR; o += kTcEpilogue) col_e[o] = o < a.M ? a.ea[a.a_mat[tile.group] * a.ea_ld + o] : 0;
+        const int pc = q * 32 + lane;
+        const bool pok = pc < tile.ncol;
+        const long long dst = pok ? a.dst_off[tile.col0 + pc] : 0;
+        const int ebv = pok ? a.eb[a.src_vec[tile.col0 + pc]] : 0;
+        const bool acc_ok = mbar_wait(&accbar[0], (unsigned)it & 1u, &abort_sh);
+        // uniform over the epilogue group (also publishes the row exponents written above)
+        if (!epi_all(acc_ok && !abort_sh)) {
+          abort_sh = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n");
+#pragma unroll 1
+        for (int cb = part; cb < TR / 16; cb += kTcEpiParts) {
+          if (cb * 16 >= a.M) break;
+          float vv[kAcc][16];
+#pragma unroll
+          for (int w = 0; w < kAcc; ++w) {
+            const unsigned taddr = tmem + ((unsigned)(q * 32) << 16) + (unsigned)(w * TR + cb * 16);
+            unsigned rr[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                  "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+                  "=r"(rr[14]), "=r"(rr[15])
+                : "r"(taddr));
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) vv[w][cc] = __uint_as_float(rr[cc]);
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n");
+          if (a.out_mode != 2 && cb * 16 + 16 <= a.M) {
+            // a full block of 16 outputs: each lane forms its 8-byte values (double-float slot or
+            // FP64), eight at a time, into the warp's staging rows; then lanes 8 g .. 8 g + 7 store
+            // eight consecutive outputs of destination 4 i + g, four destinations per instruction
+            double (*stg)[8] = stage[(warp - kTcProducers / 32)];
+#pragma unroll
+            for (int c8 = 0; c8 < 16; c8 += 8) {
+#pragma unroll
+              for (int cc = 0; cc < 8; ++cc) {
+                const int o = cb * 16 + c8 + cc;
+                float h, l;
+                fold4(vv[0][c8 + cc], vv[1][c8 + cc], vv[2][c8 + cc], vv[3][c8 + cc], h, l);
+                stg[lane][cc] = out_value(a, h, l, col_e[o] + ebv);
+              }
+              __syncwarp();
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const int src = 4 * i + (lane >> 3);
+                const long long d = __shfl_sync(0xffffffffu, dst, src);
+                if (q * 32 + src < tile.ncol)
+                  reinterpret_cast<double*>(a.Y)[d + cb * 16 + c8 + (lane & 7)] = stg[src][lane & 7];
+              }
+              __syncwarp();
+            }
+          } else if (pok && a.out_mode != 2) {
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) {
+              const int o = cb * 16 + cc;
+              if (o >= a.M) break;
+              float h, l;
+              fold4(vv[0][cc], vv[1][cc], vv[2][cc], vv[3][cc], h, l);
+              store_out(a, dst, o, h, l, col_e[o] + ebv, 0.0);
+            }
+          } else if (pok) {
+            // accumulating launch: fold, read the old values of eight outputs together, store
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc) {
+              float h, l;
+              fold4(vv[0][cc], vv[1][cc], vv[2][cc], vv[3][cc], h, l);
+              vv[0][cc] = h;
+              vv[1][cc] = l;
+            }
+#pragma unroll
+            for (int c8 = 0; c8 < 16; c8 += 8) {
+              double old[8];
+#pragma unroll
+              for (int cc = 0; cc < 8; ++cc) {
+                const int o = cb * 16 + c8 + cc;
+                old[cc] = o < a.M ? reinterpret_cast<const double*>(a.Y)[dst + o] : 0.0;
+              }
+#pragma unroll
+              for (int cc = 0; cc < 8; ++cc) {
+                const int o = cb * 16 + c8 + cc;
+                if (o < a.M) store_out(a, dst, o, vv[0][c8 + cc], vv[1][c8 + cc], col_e[o] + ebv, old[cc]);
+              }
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n");
+        mbar_arrive(&tmem_free[0]);
+        asm volatile("bar.sync 1, %0;\n" ::"n"(kTcEpilogue) : "memory");
+      }
+    } else {
+
     const int e = tid - kTcProducers;
     // warp w reads tensor-memory lanes 32 (w % 4) .. + 31; the kTcEpiParts warps of a quadrant share
     // its column blocks
@@ -716,10 +850,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       // column metadata of this tile no longer needed by any epilogue thread
       asm volatile("bar.sync 1, %0;\n" ::"n"(kTcEpilogue) : "memory");
     }
+    }
   } else if (lane == 0) {
     // ---- MMA issuer
-    // instruction descriptor: D f32, A and B bf16, both K-major, N = BN, M = 128
-    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(BN >> 3) << 17) |
+    // instruction descriptor: D f32, A and B bf16, both K-major, M = 128, N = BN (TR for transposed
+    // tiles)
+    constexpr int kN = TR ? TR : BN;
+    const unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(kN >> 3) << 17) |
                            ((unsigned)(kSplitBM >> 4) << 24);
     // shared-memory descriptors of stage 0, slice 0; the start address (16-byte units, low bits) of
     // any other slice tile is an added constant, so a K step issues its S(S+1)/2 MMAs from
@@ -754,8 +891,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const unsigned long long db = dB0 + (unsigned long long)((st * S * kTcB * 2) >> 4);
         // the first product of each accumulator in a tile (step 0, i = 0, j = w) overwrites it
         const unsigned acc = tmem + (unsigned)(buf * kAccCols);
-        if (k == 0) mma_kstep<S, BN, true>(acc, da, db, idesc);
-        else mma_kstep<S, BN, false>(acc, da, db, idesc);
+        constexpr int kSA = (kSplitBM * 16 * 2) >> 4, kSB = (BN * 16 * 2) >> 4;  // slice tile strides
+        if constexpr (TR > 0) {
+          // gathered vectors as A (128 rows), operator slices as B (its first TR rows)
+          if (k == 0) mma_kstep<S, TR, kSB, kSA, true>(acc, db, da, idesc);
+          else mma_kstep<S, TR, kSB, kSA, false>(acc, db, da, idesc);
+        } else {
+          if (k == 0) mma_kstep<S, BN, kSA, kSB, true>(acc, da, db, idesc);
+          else mma_kstep<S, BN, kSA, kSB, false>(acc, da, db, idesc);
+        }
         umma_commit(&empty[st]);
       }
       if (ok) umma_commit(&accbar[buf]);
@@ -899,10 +1043,14 @@ int prepare_split_launch() {
                            (int)mma_smem_bytes(kSplitSlices, 128, 64)));
   TRY(cudaFuncSetAttribute(k_split_gemm<kSplitSlices, 64, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)mma_smem_bytes(kSplitSlices, 64, 32)));
-  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices, 128, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_bytes(kSplitSlices, 128)));
-  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices, 64, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)tc_smem_bytes(kSplitSlices, 64)));
+  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices, 128, 96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes(kSplitSlices, 128)));
+  TRY(cudaFuncSetAttribute(k_split_gemm_tc<kSplitSlices, 128, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tc_smem_bytes(kSplitSlices, 128)));
   int sms = 0;
   TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   g_num_sms = sms > 0 ? sms : 1;
@@ -934,15 +1082,21 @@ int launch_split_gemm(const SplitArgs& a, int n_tiles, cudaStream_t s, int engin
     if (rc) return rc;
   }
   if (n_tiles <= 0) return VP_OK;
-  if (engine == kEngineTcgen05 || engine == kEngineTcgen05N64) {
+  // transposed tiles need an operator of at most 128 rows; taller ones run on the 128 x 128 engine
+  if (engine == kEngineTcgen05T && a.M > 128) engine = kEngineTcgen05;
+  if (engine == kEngineTcgen05 || engine == kEngineTcgen05N64 || engine == kEngineTcgen05T) {
     // short_ctas: two tiles per CTA (CTAs end often enough for the far-field chain's launches to find
     // SMs, and the per-CTA setup is paid half as often: 7.00 vs 7.17 ms per overlapped evaluation of
     // the full-size star, 7.07 with four)
     const int grid = short_ctas ? (n_tiles + 1) / 2 : (n_tiles < g_num_sms ? n_tiles : g_num_sms);
     if (engine == kEngineTcgen05)
-      k_split_gemm_tc<kSplitSlices, 128><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 128), s>>>(a, n_tiles);
+      k_split_gemm_tc<kSplitSlices, 128, 0><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 128), s>>>(a, n_tiles);
+    else if (engine == kEngineTcgen05N64)
+      k_split_gemm_tc<kSplitSlices, 64, 0><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 64), s>>>(a, n_tiles);
+    else if (a.M <= 96)
+      k_split_gemm_tc<kSplitSlices, 128, 96><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 128), s>>>(a, n_tiles);
     else
-      k_split_gemm_tc<kSplitSlices, 64><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 64), s>>>(a, n_tiles);
+      k_split_gemm_tc<kSplitSlices, 128, 128><<<grid, kTcThreads, tc_smem_bytes(kSplitSlices, 128), s>>>(a, n_tiles);
   }
   else if (engine == kEngineMmaSmall)
     k_split_gemm<kSplitSlices, 64, 32><<<n_tiles, 64, mma_smem_bytes(kSplitSlices, 64, 32), s>>>(a);

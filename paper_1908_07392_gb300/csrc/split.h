@@ -69,13 +69,15 @@ struct DFReduceArgs {
 // memory on 128 x 128 tiles, mma.sync on 64 x 32 tiles (four times the CTAs of the first: for the
 // small, latency-bound launches of the coarse levels), and tcgen05 on 128 x 64 tiles with two
 // accumulator sets in tensor memory (the epilogue of a tile overlaps the MMAs of the next: for
-// contractions with short K, whose tiles are bound by the epilogue). vp_autotune chooses per launch
-// shape.
-constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1, kEngineMmaSmall = 2, kEngineTcgen05N64 = 3;
-constexpr int kEngines = 4;
-constexpr int kSplitBM = 128;                             // rows of a table tile (the tiled layout's unit)
-constexpr int kSplitBMe[kEngines] = {128, 128, 64, 128};  // rows per GEMM tile, by engine
-constexpr int kSplitBN[kEngines] = {64, 128, 32, 64};     // columns per GEMM tile, by engine
+// contractions with short K, whose tiles are bound by the epilogue), and tcgen05 on transposed 128 x
+// 128 tiles (columns as the MMA's 128 rows, operator rows as its N: for operators of at most 128
+// rows, whose own rows would leave tensor-memory lanes idle). vp_autotune chooses per launch shape.
+constexpr int kEngineMmaSync = 0, kEngineTcgen05 = 1, kEngineMmaSmall = 2, kEngineTcgen05N64 = 3,
+              kEngineTcgen05T = 4;
+constexpr int kEngines = 5;
+constexpr int kSplitBM = 128;                                  // rows of a table tile (the tiled layout's unit)
+constexpr int kSplitBMe[kEngines] = {128, 128, 64, 128, 128};  // rows per GEMM tile, by engine
+constexpr int kSplitBN[kEngines] = {64, 128, 32, 64, 128};     // columns per GEMM tile, by engine
 
 int build_split(vp_tables_s* T, cudaStream_t s);
 void free_split_tables(vp_tables_s* T);

@@ -46,6 +46,11 @@ def _split_engines(w):
         torch.cuda.synchronize()
         V.vp_device_status()
         out["tcgen05_n64"] = (u3.cpu().numpy(), g3[0].cpu().numpy(), g3[1].cpu().numpy())
+        V.vp_tree_set_engine(vp.tree, V.ENGINE_TCGEN05_T)
+        u4, g4 = vp(f)
+        torch.cuda.synchronize()
+        V.vp_device_status()
+        out["tcgen05_t"] = (u4.cpu().numpy(), g4[0].cpu().numpy(), g4[1].cpu().numpy())
         return out
     finally:
         vp.close()
