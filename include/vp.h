@@ -331,7 +331,7 @@ void vp_periodic_free(vp_periodic plan);
  *  about (2 K^2 + 12) n^2 doubles; synchronises `stream`).
  * vp_sdc_set -- the state at the first time: u0 device [2][n][n], its gradient gradu0 [2][2][n][n]
  *  (gradu0[a][m] = d u_a / d x_m) and its Laplacian lap0 [2][n][n] (the paper supplies Laplacian u at the
- *  initial time, Sec. 3.3). Must precede vp_sdc_step.
+ *  initial time, Sec. 3.3). Must precede vp_sdc_step and vp_sdc_get (VP_ERR_ARG otherwise).
  * vp_sdc_step -- advances n_steps steps of Delta t, all on `stream` without host synchronisation.
  * vp_sdc_get -- copies the current u [2][n][n] and its gradient [2][2][n][n] (device).
  * Calls on one stepper must not overlap on the GPU.

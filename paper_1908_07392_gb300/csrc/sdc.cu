@@ -118,6 +118,7 @@ struct vp_sdc_s {
   double* F = nullptr;                        // [2][nn]
   double* G = nullptr;                        // [2][2][nn]: gradient of the latest solve
   double w[kMaxOrder][kMaxNodes] = {};
+  bool has_state = false;                     // vp_sdc_set has been called
 };
 
 namespace {
@@ -224,11 +225,12 @@ extern "C" int vp_sdc_set(vp_sdc S, const double* u0, const double* gradu0, cons
   // N of the initial state
   k_sdc_post<<<grid_for(S->nn), 256, 0, s>>>(S->nn, S->alpha2, S->state[0], S->G, nullptr, S->state[1], nullptr);
   TRY(cudaGetLastError());
+  S->has_state = true;
   return VP_OK;
 }
 
 extern "C" int vp_sdc_step(vp_sdc S, int n_steps, void* stream) {
-  if (!S || n_steps < 0) return VP_ERR_ARG;
+  if (!S || n_steps < 0 || !S->has_state) return VP_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < n_steps; ++i) {
     const int rc = one_step(S, s);
@@ -238,7 +240,7 @@ extern "C" int vp_sdc_step(vp_sdc S, int n_steps, void* stream) {
 }
 
 extern "C" int vp_sdc_get(vp_sdc S, double* u, double* gradu, void* stream) {
-  if (!S || !u || !gradu) return VP_ERR_ARG;
+  if (!S || !u || !gradu || !S->has_state) return VP_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes2 = (size_t)2 * S->nn * sizeof(double);
   TRY(cudaMemcpyAsync(u, S->state[0], bytes2, cudaMemcpyDeviceToDevice, s));

@@ -75,6 +75,14 @@ def test_order_on_interacting_modes():
 
 
 def test_bad_arguments():
+    s = V.SISDC(10.0, 0.01, 2, 64, L)
+    try:
+        with pytest.raises(V.VPError):      # no state set yet
+            s.step(1)
+        with pytest.raises(V.VPError):
+            s.get()
+    finally:
+        s.close()
     with pytest.raises(V.VPError):
         V.SISDC(10.0, 0.01, 5, 64, L)
     with pytest.raises(V.VPError):
